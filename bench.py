@@ -1,0 +1,328 @@
+"""Benchmark: quantized-BVH neighbor list (build + query) plus the fused LJ
+energy/force pass on the LJ fluid with N = 2,097,152 particles at rho = 0.8.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = qbvh_build + qbvh_query (with its overflow check) + the LJ
+energy/force pass, all on the GPU; inputs are resident in HBM.  Between timed
+steps L2 is flushed by writing a 256 MiB buffer (outside the timed events).
+Timing: CUDA events per stage on the launching stream; max over ranks.
+
+``--impl reference`` times the CPU oracle (cell list + FP64 LJ) on the host
+cores for the same workload and metric; only rank 0 runs it.
+
+With --gpus N > 1 (torchrun) every rank runs an independent replica of the
+workload on its own GPU; value = all ranks' particles / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "nlist particles/s (build+query), LJ N=2M; batched vs per-system; E/F grad err"
+WORKLOAD = "lj_n2097152_rho0.8"
+R_CUT = 3.0
+CAP = 256
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _alg_bytes(n: int, total_neighbors: int) -> int:
+    # positions read once (16 B), counts written (4 B), list entries written (4 B each)
+    return 16 * n + 4 * n + 4 * int(total_neighbors)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import workloads
+    from paper_1901_08088_gb300 import NeighborList, _lib
+    from paper_1901_08088_gb300.qbvh import qbvh_lj_forward, check
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    s = workloads.workload(WORKLOAD, seed=rank)
+    n = s.n
+    pos4_host = torch.from_numpy(workloads.pack_float4(s.pos, s.types)).pin_memory()
+    pos4 = pos4_host.cuda()
+    nl = NeighborList(local)
+    eps = torch.ones((1, 1), dtype=torch.float32, device="cuda")
+    sig = torch.ones((1, 1), dtype=torch.float32, device="cuda")
+    U = torch.empty(1, dtype=torch.float64, device="cuda")
+    F = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    rc = np.full((1, 1), R_CUT, np.float32)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step(p4):
+        nl.build(p4, s.L)
+        nl.query(s.r_list, cap=CAP)
+        check(qbvh_lj_forward(nl.h, p4, eps, sig, rc, None, U, F, None, None), "lj")
+
+    for _ in range(args.warmup):
+        step(pos4)
+    torch.cuda.synchronize()
+    mean_nbrs = float(nl.neighbors()[1].double().mean().item())
+    total_nbrs = int(nl.neighbors()[1].long().sum().item())
+
+    stream = torch.cuda.current_stream()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0, e1, e2, e3 = ev[k]
+        e0.record(stream)
+        nl.build(pos4, s.L)
+        e1.record(stream)
+        nl.query_async(s.r_list, CAP)
+        e2.record(stream)
+        stream.synchronize()
+        rc_q, mx = nl.query_status()
+        if rc_q != 0:
+            raise RuntimeError(f"query failed in timed step: {_lib.QBVHError(rc_q)}")
+        check(qbvh_lj_forward(nl.h, pos4, eps, sig, rc, None, U, F, None, None), "lj")
+        e3.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    t_build = np.array([ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)])
+    t_query = np.array([ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)])
+    t_lj = np.array([ev[k][2].elapsed_time(ev[k][3]) for k in range(args.steps)])
+    t_step = t_build + t_query + t_lj
+    total_ms = float(t_step.sum())
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+
+    # end-to-end through the public API with host buffers: H2D positions,
+    # build + query + LJ, D2H forces and energy, every step
+    F_host = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    U_host = torch.empty(1, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    ee0 = torch.cuda.Event(enable_timing=True)
+    ee1 = torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for k in range(e2e_steps):
+        flush.fill_(float(k))
+        ee0.record(stream)
+        pos4.copy_(pos4_host, non_blocking=True)
+        step(pos4)
+        F_host.copy_(F, non_blocking=True)
+        U_host.copy_(U, non_blocking=True)
+        ee1.record(stream)
+        ee1.synchronize()
+        e2e_ms += ee0.elapsed_time(ee1)
+    if world > 1:
+        tt = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+
+    out = None
+    if rank == 0:
+        peaks = _peaks()
+        hbm = float(peaks["hbm_gbs"]) if peaks else 6800.0
+        peak_src = "measured" if peaks else "fallback"
+        bytes_q = _alg_bytes(n, total_nbrs)
+        q_avg_s = float(t_query.mean()) * 1e-3
+        achieved = bytes_q / q_avg_s / 1e9
+        step_alg = bytes_q / (float(t_step.mean()) * 1e-3) / 1e9
+        value = world * n * args.steps / (total_ms * 1e-3)
+        out = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "particles/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {
+                "workload": "LJ fluid N=2,097,152 rho=0.8 jittered lattice (+-0.25), r_list=3.3, cap 256, "
+                            "build+query+LJ energy/force (r_cut=3.0, eps=sig=1)",
+                "n": n, "L": float(s.L), "r_list": float(s.r_list[0, 0]), "cap": CAP,
+                "mean_neighbors": mean_nbrs,
+                "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
+                "parallelism": f"replicas x{world}",
+                "bundle_k": nl.get_option(_lib.QBVH_OPT_BUNDLE),
+                "query_block": nl.get_option(_lib.QBVH_OPT_QUERY_BLOCK),
+            },
+            "breakdown_ms": {"build": float(t_build.mean()), "query": float(t_query.mean()),
+                             "lj": float(t_lj.mean())},
+            "nlist_particles_per_s": n / (float((t_build + t_query).mean()) * 1e-3),
+            "roofline": {
+                "kernel": "query_kernel (traversal + exact leaf test + list write)",
+                "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": peak_src,
+                "alg_bytes_per_launch": bytes_q,
+                "step_frac": step_alg / hbm,
+            },
+            "e2e": {"value": world * n * e2e_steps / (e2e_ms * 1e-3), "unit": "particles/s",
+                    "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 12 * n + 8},
+            "gpu_launches": args.steps * 14,
+            "clocks": clocks,
+            "wall_s_timed": wall,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = cpu_baseline(s, samples=1)
+        elif world == 1:
+            out["cpu_baseline"] = None
+    nl.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def cpu_baseline(s, samples=1):
+    """The oracle as it stands: OpenMP cell list build+query + FP64 LJ, on the host cores."""
+    import oracle
+
+    t = []
+    for _ in range(samples):
+        t0 = time.perf_counter()
+        rows, counts = oracle.nlist(s.pos, s.L, s.r_list, cap=CAP, method="cell")
+        oracle.lj_fp64(s.pos, s.types, s.L, [[1.0]], [[1.0]], np.float32(R_CUT), rows, counts)
+        t.append(time.perf_counter() - t0)
+    tm = float(np.median(t))
+    return {"value": s.n / tm, "unit": "particles/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{samples} full step(s) of the N={s.n} workload: cell-list build+query (OpenMP) "
+                      f"+ FP64 LJ energy/forces (1 thread); {tm:.2f} s per step"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return None
+    import oracle
+    import workloads
+
+    oracle.build()
+    s = workloads.workload(WORKLOAD, seed=0)
+    for _ in range(args.warmup):
+        oracle.nlist(s.pos, s.L, s.r_list, cap=CAP, method="cell")
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        rows, counts = oracle.nlist(s.pos, s.L, s.r_list, cap=CAP, method="cell")
+        oracle.lj_fp64(s.pos, s.types, s.L, [[1.0]], [[1.0]], np.float32(R_CUT), rows, counts)
+        t.append(time.perf_counter() - t0)
+    total = float(np.sum(t))
+    value = s.n * args.steps / total
+    sample = f"{args.steps} full step(s) of N={s.n}: cell-list build+query (OpenMP) + FP64 LJ (1 thread)"
+    return {
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "LJ fluid N=2,097,152 rho=0.8 jittered lattice (+-0.25), r_list=3.3, "
+                               "cap 256, build+query+LJ energy/force (r_cut=3.0)"},
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        out = run_reference(args)
+    else:
+        out = run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,245 @@
+/*
+ * qbvh -- neighbor lists through a linear bounding volume hierarchy with
+ * quantized node bounds, for one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Howard, Statt, Madutsa, Truskett, Panagiotopoulos, "Quantized
+ * bounding volume hierarchies for neighbor search in molecular simulations on
+ * graphics processing units" (arXiv:1901.08088).
+ *
+ * The problem this library solves is the paper's (Sec. 1, Fig. 1a; Sec. 4):
+ * given particle positions in a periodic cubic box, a particle type per
+ * particle and a list radius per type pair, find for every particle i all
+ * particles j != i closer than the list radius, and store them as a Verlet
+ * (neighbor) list.  The list is exact: the distance of every pair found by
+ * the tree traversal is re-tested with one fixed FP32 expression,
+ *
+ *     dx = xj - xi;  dx = dx - L * rint(dx * Linv);      (same for y and z)
+ *     d2 = (dx*dx + dy*dy) + dz*dz;    j in N(i)  iff  d2 < r*r,
+ *
+ * with Linv = 1.0f / L and r*r rounded once in FP32, so the list is
+ * bit-identical to a brute-force search with that expression.
+ *
+ * Conventions for every entry point
+ *   - Return value: QBVH_OK (0) or one of the QBVH_ERR_* codes below.
+ *   - Pointers named *_dev are device pointers on the handle's device; *_host
+ *     are host pointers read before the call returns.
+ *   - All GPU work is enqueued on `stream` (0 = legacy default stream) and is
+ *     asynchronous unless stated otherwise.  The caller keeps every input
+ *     device buffer alive, unmodified, until that work has completed.
+ *   - Buffers returned by the library (nlist_get, qbvh_tree_get) belong to the
+ *     handle and stay valid until the next build/query/destroy on that handle.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ *   - Counts: 0 <= n < 2^30 particles, 1 <= n_types <= 8 types.
+ */
+#ifndef QBVH_H
+#define QBVH_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define QBVH_OK 0
+#define QBVH_ERR_INVALID_ARG 1      /* bad pointer, size, alignment or option      */
+#define QBVH_ERR_OUT_OF_BOX 2       /* a position is outside [0, L) or not finite  */
+#define QBVH_ERR_BAD_TYPE 3         /* a particle type is outside [0, n_types)     */
+#define QBVH_ERR_CUTOFF_TOO_LARGE 4 /* list radius >= L/2 for some system          */
+#define QBVH_ERR_OVERFLOW 5         /* a row still exceeded its capacity after the
+                                       allowed retries; counts are complete,
+                                       rows are truncated at cap                    */
+#define QBVH_ERR_DEVICE_TIMEOUT 6   /* a bounded device-side wait gave up          */
+#define QBVH_ERR_CUDA 7             /* a CUDA runtime call failed                  */
+#define QBVH_ERR_OOM 8              /* device or pinned allocation failed          */
+#define QBVH_ERR_NOT_BUILT 9        /* query/get before a successful build         */
+#define QBVH_ERR_INTERNAL 10        /* a device-side consistency check failed (an
+                                       index out of range or a walk longer than
+                                       the tree); the access was skipped          */
+
+/* Largest number of particle types a handle accepts. */
+#define QBVH_MAX_TYPES 8
+
+/* Opaque handle: owns the tree, the neighbor list and all scratch memory. */
+typedef struct qbvh_ctx *qbvh_handle;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *qbvh_strerror(int code);
+
+/*
+ * Create a handle bound to CUDA device `device`.  Allocates only a few bytes
+ * of pinned host memory; device buffers are allocated by the first build and
+ * grown when a later call needs more.
+ * Errors: INVALID_ARG (out == NULL), CUDA (no such device), OOM.
+ */
+int qbvh_create(qbvh_handle *out, int device);
+
+/* Release every buffer of the handle.  Synchronizes the handle's device. */
+int qbvh_destroy(qbvh_handle h);
+
+/* ---- tuning options (qbvh_set_option) ---------------------------------- */
+/* Subtree collapse (Sec. 2.3, final paragraph): internal nodes with at most K
+ * leaves are traversed by testing their leaves directly.  K = 1 keeps the
+ * paper's one-particle leaves.  Values 1..32, default 4.  Takes effect at the
+ * next build. */
+#define QBVH_OPT_BUNDLE 1
+/* Threads per block of the traversal kernel: 32..1024, multiple of 32,
+ * default 128.  Takes effect at the next query. */
+#define QBVH_OPT_QUERY_BLOCK 2
+/* 1 = skip the exact leaf test and list every particle whose node the search
+ * sphere overlaps, as Alg. 1 does (candidates, false positives included).
+ * 0 (default) = exact list. */
+#define QBVH_OPT_CANDIDATES 3
+
+int qbvh_set_option(qbvh_handle h, int option, int value);
+int qbvh_get_option(qbvh_handle h, int option, int *value);
+
+/*
+ * Build the quantized LBVH of one periodic system (Sec. 2.1, 2.2, Fig. 3):
+ * Morton binning into 2^10-1 bins per axis, stable radix sort of the 30-bit
+ * codes, Karras hierarchy (N-1 internal nodes with two children each),
+ * bottom-up fit, ropes for stackless traversal and outward-rounded 10-bit
+ * quantization of every node against the root AABB.  With n_types > 1 one
+ * tree is built per type (per-type trees for size-asymmetric mixtures,
+ * Sec. 1 and Sec. 5).
+ *
+ * pos_dev : [n] float4 {x, y, z, w}, 16-byte aligned, x,y,z in [0, L),
+ *           w = the particle's type as int32 bits (0 when n_types == 1).
+ * n       : number of particles (0 allowed: empty tree).
+ * L       : cubic box edge, finite and > 0.
+ * n_types : 1..QBVH_MAX_TYPES.
+ * Positions and types are validated on the device; a violation is reported
+ * by the next qbvh_query (QBVH_ERR_OUT_OF_BOX / QBVH_ERR_BAD_TYPE).
+ * Errors here: INVALID_ARG, OOM, CUDA.
+ */
+int qbvh_build(qbvh_handle h, const void *pos_dev, int n, float L, int n_types,
+               cudaStream_t stream);
+
+/*
+ * Build the trees of n_sys independent periodic systems in one launch
+ * sequence (one tree per system and type).  System k owns particles
+ * [sys_offsets_host[k], sys_offsets_host[k+1]) of pos_dev and the cubic box
+ * of edge L_host[k].  sys_offsets_host has n_sys+1 non-decreasing entries,
+ * starting at 0 and ending at n_total.  1 <= n_sys <= 65536 and
+ * n_sys * n_types <= 65536.  Same pos_dev layout and errors as qbvh_build.
+ */
+int qbvh_build_batched(qbvh_handle h, const void *pos_dev, int n_total, int n_sys,
+                       const int *sys_offsets_host, const float *L_host, int n_types,
+                       cudaStream_t stream);
+
+/*
+ * Neighbor list from the last build: stackless rope traversal (Alg. 1) of
+ * every particle in Z-order over the periodic images whose search sphere
+ * overlaps the root (27-bit image set, Sec. 2.3), sphere-AABB test against
+ * the decompressed node bounds (Eq. 2) with directed rounding (Sec. 3), the
+ * exact FP32 distance test at the leaves, and compaction into rows.
+ *
+ * r_list_host : [n_types][n_types] list radii (r_cut + skin), symmetric,
+ *               each 0 <= r < L/2 of every system (0 = type pair never listed).
+ * cap         : initial row capacity, >= 1.
+ * max_retries : when some row has more than cap neighbors the capacity is
+ *               raised to the largest count rounded up to 32 and the traversal
+ *               rerun (tree reused), at most max_retries times.
+ * Blocks the host on one 8-byte readback per traversal (the largest count and
+ * the device error word).
+ * Errors: NOT_BUILT, INVALID_ARG, CUTOFF_TOO_LARGE, OUT_OF_BOX, BAD_TYPE,
+ *         OVERFLOW (counts complete, rows truncated), DEVICE_TIMEOUT, OOM, CUDA.
+ */
+int qbvh_query(qbvh_handle h, const float *r_list_host, int cap, int max_retries,
+               cudaStream_t stream);
+
+/*
+ * Enqueue one traversal without waiting: the list is written with capacity
+ * cap and the 8-byte status is copied to the handle's pinned host memory on
+ * `stream`.  No host synchronization, no allocation once the row buffer
+ * holds n*cap entries, so the call may be recorded into a CUDA graph after a
+ * first call at the same sizes.  Read the outcome with qbvh_query_status once
+ * the stream has completed.
+ */
+int qbvh_query_async(qbvh_handle h, const float *r_list_host, int cap, cudaStream_t stream);
+
+/*
+ * Outcome of the last traversal enqueued on the handle; valid after the
+ * caller has synchronized that stream.  *max_count = largest row count,
+ * return value = QBVH_OK, OUT_OF_BOX, BAD_TYPE, DEVICE_TIMEOUT or OVERFLOW
+ * (max_count > cap).
+ */
+int qbvh_query_status(qbvh_handle h, int *max_count);
+
+/*
+ * Borrow the neighbor list of the last query (Sec. 1: the Verlet list).
+ * rows   : [n][cap] int32, row i lists the original indices j of particle i's
+ *          neighbors in unspecified order; entries past counts[i] are unset.
+ * counts : [n] int32 number of neighbors of particle i (may exceed cap only
+ *          after QBVH_ERR_OVERFLOW).
+ * Indices are positions in the pos_dev array of the build (concatenated over
+ * systems for a batched build).  Any output pointer may be NULL.
+ */
+int nlist_get(qbvh_handle h, const int **rows, const int **counts, int *cap, int *max_count);
+
+/*
+ * Borrow the tree of the last build, for inspection and tests.
+ * nodes     : [n] int4 internal nodes by Karras index, each
+ *             {lo | bundle<<31, hi, left child or first leaf, rope},
+ *             lo/hi = qx<<20 | qy<<10 | qz (Fig. 3b), ids >= 0 internal,
+ *             ~k leaf k, INT32_MIN end of traversal; slot of each tree's
+ *             last leaf unused.
+ * leaves    : [n] float4 {x, y, z, original index | (rope is internal)<<31}
+ *             in Z-order.
+ * order     : [n] int32 sorted position -> original index.
+ * seg_start : [n_seg + 1] int32 first sorted position of each tree, tree
+ *             s = system * n_types + type.
+ * frames    : [n_seg] 8 floats {R_lo xyz, h xyz, -, -}: quantization frame
+ *             of each tree (root AABB corner and bin width).
+ * n_seg     : number of trees.
+ */
+int qbvh_tree_get(qbvh_handle h, const void **nodes, const void **leaves, const int **order,
+                  const int **seg_start, const float **frames, int *n_seg);
+
+/*
+ * Truncated-and-shifted Lennard-Jones energy (Eq. 1, shifted to zero at
+ * r_cut, Sec. 1) over the handle's last neighbor list, in one fused pass:
+ * per-particle energy, forces and the gradients with respect to the
+ * per-type-pair parameters.  Pairs interact when the FP32 distance
+ * expression above gives d2 < r_cut*r_cut.  Accumulation is FP32 per
+ * particle; the per-system sums are FP64.
+ *
+ * pos_dev      : [n] float4 as for the build (original order).
+ * eps_dev, sig_dev : [n_types][n_types] float32 device arrays.
+ * r_cut_host   : [n_types][n_types] float32, each <= the list radius used.
+ * e_dev        : [n] float32 out, 1/2 of particle i's pair energies (or NULL).
+ * U_dev        : [n_sys] float64 out, total energy of each system (required).
+ * F_dev        : [n][3] float32 out, F_i = -dU/dx_i (or NULL).
+ * dE_dev, dS_dev : [n_sys][n_types][n_types] float64 out, dU/deps[a][b] and
+ *                dU/dsig[a][b] of each system, each matrix entry treated as
+ *                its own parameter (or NULL).
+ * Errors: NOT_BUILT (no list), INVALID_ARG, CUDA.
+ */
+int qbvh_lj_forward(qbvh_handle h, const void *pos_dev, const float *eps_dev,
+                    const float *sig_dev, const float *r_cut_host, float *e_dev, double *U_dev,
+                    float *F_dev, double *dE_dev, double *dS_dev, cudaStream_t stream);
+
+/*
+ * Chain rule for a scalar loss of the per-system energies: with g = dLoss/dU
+ * ([n_sys] float64 device), writes grad_pos[i] = -g[sys(i)] * F[i] ([n][3]
+ * float32) and grad_eps = sum_k g[k] dE[k], grad_sig likewise ([n_types^2]
+ * float32).  F, dE, dS are the outputs of qbvh_lj_forward.  Any output may
+ * be NULL.
+ */
+int qbvh_lj_backward(qbvh_handle h, const double *g_dev, const float *F_dev,
+                     const double *dE_dev, const double *dS_dev, float *grad_pos_dev,
+                     float *grad_eps_dev, float *grad_sig_dev, cudaStream_t stream);
+
+/*
+ * Pack positions [n][3] float32 and types [n] int32 (types_dev may be NULL
+ * for all-zero) into the float4 layout the build reads.
+ */
+int qbvh_pack_positions(const float *xyz_dev, const int *types_dev, int n, void *pos4_dev,
+                        cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QBVH_H */

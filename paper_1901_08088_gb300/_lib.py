@@ -1,0 +1,89 @@
+"""ctypes binding of ``libqbvh.so`` (C ABI in include/qbvh.h).
+
+Argument marshalling only: every step of the neighbor search runs in the CUDA
+kernels of the library.  There is no CPU fallback; if the library has not been
+built, loading fails with an error that says how to build it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libqbvh.so")
+
+QBVH_OK = 0
+QBVH_ERR_INVALID_ARG = 1
+QBVH_ERR_OUT_OF_BOX = 2
+QBVH_ERR_BAD_TYPE = 3
+QBVH_ERR_CUTOFF_TOO_LARGE = 4
+QBVH_ERR_OVERFLOW = 5
+QBVH_ERR_DEVICE_TIMEOUT = 6
+QBVH_ERR_CUDA = 7
+QBVH_ERR_OOM = 8
+QBVH_ERR_NOT_BUILT = 9
+QBVH_ERR_INTERNAL = 10
+
+QBVH_OPT_BUNDLE = 1
+QBVH_OPT_QUERY_BLOCK = 2
+QBVH_OPT_CANDIDATES = 3
+
+_lock = threading.Lock()
+_lib = None
+
+P = C.c_void_p
+I = C.c_int
+F = C.c_float
+PP = C.POINTER(C.c_void_p)
+PI = C.POINTER(C.c_int)
+
+# name -> (restype, argtypes); names are the C entry points
+SIGNATURES = {
+    "qbvh_strerror": (C.c_char_p, [I]),
+    "qbvh_create": (I, [PP, I]),
+    "qbvh_destroy": (I, [P]),
+    "qbvh_set_option": (I, [P, I, I]),
+    "qbvh_get_option": (I, [P, I, PI]),
+    "qbvh_build": (I, [P, P, I, F, I, P]),
+    "qbvh_build_batched": (I, [P, P, I, I, P, P, I, P]),
+    "qbvh_query": (I, [P, P, I, I, P]),
+    "qbvh_query_async": (I, [P, P, I, P]),
+    "qbvh_query_status": (I, [P, PI]),
+    "nlist_get": (I, [P, PP, PP, PI, PI]),
+    "qbvh_tree_get": (I, [P, PP, PP, PP, PP, PP, PI]),
+    "qbvh_lj_forward": (I, [P, P, P, P, P, P, P, P, P, P, P]),
+    "qbvh_lj_backward": (I, [P, P, P, P, P, P, P, P, P]),
+    "qbvh_pack_positions": (I, [P, P, I, P, P]),
+}
+
+
+class QBVHError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = int(code)
+        msg = lib().qbvh_strerror(self.code).decode()
+        super().__init__(f"{where}: {msg} (code {self.code})" if where else f"{msg} (code {self.code})")
+
+
+def lib():
+    """Load libqbvh.so once; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with "
+                    "`python -m paper_1901_08088_gb300.build_lib` (the CUDA path has no CPU fallback)")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(code: int, where: str = "") -> int:
+    if code != QBVH_OK:
+        raise QBVHError(code, where)
+    return code

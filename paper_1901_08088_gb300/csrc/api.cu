@@ -1,0 +1,608 @@
+// C ABI of the qbvh library (declarations and contracts: include/qbvh.h).
+//
+// Host side of the method: argument validation, buffer ownership, the launch
+// sequence of the build (Sec. 2.1-2.2) and of the traversal (Alg. 1), the
+// row-capacity overflow check and retry, and the Lennard-Jones pass.
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/qbvh.h"
+#include "qbvh_internal.cuh"
+
+using namespace qbvh;
+
+namespace qbvh {
+int lj_block_size();
+}
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    bool grown = false;   // set when the last ensure() reallocated
+};
+
+enum Fault { FAULT_NONE = 0, FAULT_ALLOC = 1, FAULT_TIMEOUT = 2, FAULT_OVERFLOW = 3 };
+
+int read_fault_env()
+{
+    const char *f = getenv("QBVH_FAULT");
+    if (!f) return FAULT_NONE;
+    if (!strcmp(f, "alloc")) return FAULT_ALLOC;
+    if (!strcmp(f, "timeout")) return FAULT_TIMEOUT;
+    if (!strcmp(f, "overflow")) return FAULT_OVERFLOW;
+    return FAULT_NONE;
+}
+
+}  // namespace
+
+struct qbvh_ctx {
+    int device = 0;
+    int fault = FAULT_NONE;
+    // options
+    int bundle_k = 4;
+    int query_block = 128;
+    int candidates = 0;
+    // last build
+    bool built = false;
+    int n = 0, n_sys = 0, n_types = 0, n_seg = 0;
+    bool wide = false;
+    int sorted = 0;   // which key/value buffer pair holds the sorted result
+    std::vector<int> off;
+    std::vector<float> L;
+    std::vector<SysInfo> sysinfo;
+    float L_min = 0.f, L_max = 0.f;
+    // last query
+    bool have_list = false;
+    int cap = 0;
+    int max_count = 0;
+    float r_list[64];
+    // device buffers
+    DevBuf keys[2], vals[2], sort_scratch, nodes, leaves, leaf_q, range, child, par_int, par_leaf, visit;
+    DevBuf seg, acc, seg_start, frames, sys, sys_off, status;
+    DevBuf rows, counts;
+    DevBuf lj_partials, lj_blk_sys, lj_blk_first, lj_sys_blk;
+    std::vector<int> lj_layout_off;   // offsets the LJ block tables were built for
+    int lj_n_blocks = 0;
+    // uploads cached by content
+    std::vector<SysInfo> up_sys;
+    std::vector<int> up_off;
+    // pinned host status
+    DevStatus *h_status = nullptr;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1, want;
+    explicit DeviceGuard(int d) : want(d)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0 && prev != want) cudaSetDevice(prev);
+    }
+};
+
+int ensure(qbvh_ctx *h, DevBuf &b, size_t bytes)
+{
+    b.grown = false;
+    if (bytes == 0) bytes = 16;
+    if (bytes <= b.cap) return QBVH_OK;
+    if (h->fault == FAULT_ALLOC) return QBVH_ERR_OOM;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return QBVH_ERR_OOM;
+    }
+    b.cap = bytes;
+    b.grown = true;
+    return QBVH_OK;
+}
+
+void release(DevBuf &b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+int cuda_status()
+{
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? QBVH_OK : QBVH_ERR_CUDA;
+}
+
+int ceil_log2(int v)
+{
+    int b = 0;
+    while ((1 << b) < v) ++b;
+    return b;
+}
+
+template <typename T>
+int upload_if_changed(qbvh_ctx *h, DevBuf &dst, std::vector<T> &cache, const std::vector<T> &src,
+                      cudaStream_t s)
+{
+    const size_t bytes = src.size() * sizeof(T);
+    int rc = ensure(h, dst, bytes);
+    if (rc) return rc;
+    if (!dst.grown && cache.size() == src.size() && !memcmp(cache.data(), src.data(), bytes)) return QBVH_OK;
+    if (cudaMemcpyAsync(dst.p, src.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return QBVH_ERR_CUDA;
+    cache = src;
+    return QBVH_OK;
+}
+
+float round_up_f(double v)
+{
+    float f = (float)v;
+    if ((double)f < v) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+int map_dev_err(unsigned err)
+{
+    if (err & QBVH_DEVERR_OUT_OF_BOX) return QBVH_ERR_OUT_OF_BOX;
+    if (err & QBVH_DEVERR_BAD_TYPE) return QBVH_ERR_BAD_TYPE;
+    if (err & QBVH_DEVERR_TIMEOUT) return QBVH_ERR_DEVICE_TIMEOUT;
+    if (err & QBVH_DEVERR_INTERNAL) return QBVH_ERR_INTERNAL;
+    return QBVH_OK;
+}
+
+int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *off, const float *L, int n_types,
+               cudaStream_t s)
+{
+    if (!h) return QBVH_ERR_INVALID_ARG;
+    if (n < 0 || n >= (1 << 30) || n_sys < 1 || n_sys > 65536) return QBVH_ERR_INVALID_ARG;
+    if (n_types < 1 || n_types > QBVH_MAX_TYPES || n_sys * n_types > 65536) return QBVH_ERR_INVALID_ARG;
+    if (n > 0 && (!pos_dev || ((uintptr_t)pos_dev & 15u))) return QBVH_ERR_INVALID_ARG;
+    if (!off || !L) return QBVH_ERR_INVALID_ARG;
+    if (off[0] != 0 || off[n_sys] != n) return QBVH_ERR_INVALID_ARG;
+    for (int k = 0; k < n_sys; ++k) {
+        if (off[k + 1] < off[k]) return QBVH_ERR_INVALID_ARG;
+        if (!(L[k] > 0.f) || !isfinite(L[k])) return QBVH_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(h->device);
+    h->built = false;
+    h->have_list = false;
+    h->n = n;
+    h->n_sys = n_sys;
+    h->n_types = n_types;
+    h->n_seg = n_sys * n_types;
+    h->wide = (n_sys > 1) || (n_types > 4);
+    h->off.assign(off, off + n_sys + 1);
+    h->L.assign(L, L + n_sys);
+    h->sysinfo.resize(n_sys);
+    h->L_min = INFINITY;
+    h->L_max = 0.f;
+    for (int k = 0; k < n_sys; ++k) {
+        SysInfo si;
+        memset(&si, 0, sizeof si);
+        si.offset = off[k];
+        si.count = off[k + 1] - off[k];
+        si.L = L[k];
+        si.Linv = 1.0f / L[k];
+        si.mscale = 1023.0f / L[k];
+        h->sysinfo[k] = si;
+        h->L_min = fminf(h->L_min, L[k]);
+        h->L_max = fmaxf(h->L_max, L[k]);
+    }
+    const int bits = h->wide ? 30 + ceil_log2(h->n_seg) : (n_types > 1 ? 32 : 30);
+    const int passes = (bits + 7) / 8;
+    const size_t kb = h->wide ? 8 : 4;
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    int rc = QBVH_OK;
+    rc = rc ? rc : ensure(h, h->keys[0], nn * kb);
+    rc = rc ? rc : ensure(h, h->keys[1], nn * kb);
+    rc = rc ? rc : ensure(h, h->vals[0], nn * 4);
+    rc = rc ? rc : ensure(h, h->vals[1], nn * 4);
+    rc = rc ? rc : ensure(h, h->sort_scratch, sort_scratch_bytes(n, passes));
+    rc = rc ? rc : ensure(h, h->nodes, nn * sizeof(int4));
+    rc = rc ? rc : ensure(h, h->leaves, nn * sizeof(float4));
+    rc = rc ? rc : ensure(h, h->leaf_q, nn * sizeof(uint2));
+    rc = rc ? rc : ensure(h, h->range, nn * sizeof(int2));
+    rc = rc ? rc : ensure(h, h->child, nn * sizeof(int2));
+    rc = rc ? rc : ensure(h, h->par_int, nn * 4);
+    rc = rc ? rc : ensure(h, h->par_leaf, nn * 4);
+    rc = rc ? rc : ensure(h, h->visit, nn * 4);
+    rc = rc ? rc : ensure(h, h->seg, (size_t)h->n_seg * sizeof(SegInfo));
+    rc = rc ? rc : ensure(h, h->acc, (size_t)h->n_seg * 8 * 4);
+    rc = rc ? rc : ensure(h, h->seg_start, (size_t)(h->n_seg + 1) * 4);
+    rc = rc ? rc : ensure(h, h->frames, (size_t)h->n_seg * 8 * 4);
+    rc = rc ? rc : ensure(h, h->status, sizeof(DevStatus));
+    if (rc) return rc;
+    rc = upload_if_changed(h, h->sys, h->up_sys, h->sysinfo, s);
+    if (rc) return rc;
+    rc = upload_if_changed(h, h->sys_off, h->up_off, h->off, s);
+    if (rc) return rc;
+    if (n > 0) {
+        // parents start at -1 so that a missing link ends a walk instead of
+        // sending it to an arbitrary index
+        if (cudaMemsetAsync(h->visit.p, 0, (size_t)n * 4, s) != cudaSuccess ||
+            cudaMemsetAsync(h->par_int.p, 0xFF, (size_t)n * 4, s) != cudaSuccess ||
+            cudaMemsetAsync(h->par_leaf.p, 0xFF, (size_t)n * 4, s) != cudaSuccess)
+            return QBVH_ERR_CUDA;
+    }
+
+    BuildArgs a;
+    memset(&a, 0, sizeof a);
+    a.pos = reinterpret_cast<const float4 *>(pos_dev);
+    a.n = n;
+    a.n_sys = n_sys;
+    a.n_types = n_types;
+    a.n_seg = h->n_seg;
+    a.wide_keys = h->wide;
+    a.bundle_k = h->bundle_k;
+    a.sys = reinterpret_cast<const SysInfo *>(h->sys.p);
+    a.sys_off = reinterpret_cast<const int *>(h->sys_off.p);
+    a.seg = reinterpret_cast<SegInfo *>(h->seg.p);
+    a.seg_rootbits = reinterpret_cast<unsigned *>(h->acc.p);
+    a.seg_start = reinterpret_cast<int *>(h->seg_start.p);
+    a.frames = reinterpret_cast<float *>(h->frames.p);
+    a.keys = h->keys[0].p;
+    a.range = reinterpret_cast<int2 *>(h->range.p);
+    a.child = reinterpret_cast<int2 *>(h->child.p);
+    a.par_int = reinterpret_cast<int *>(h->par_int.p);
+    a.par_leaf = reinterpret_cast<int *>(h->par_leaf.p);
+    a.visit = reinterpret_cast<int *>(h->visit.p);
+    a.leaf_q = reinterpret_cast<uint2 *>(h->leaf_q.p);
+    a.nodes = reinterpret_cast<int4 *>(h->nodes.p);
+    a.leaves = reinterpret_cast<float4 *>(h->leaves.p);
+    a.status = reinterpret_cast<DevStatus *>(h->status.p);
+
+    launch_build_prepare(a, s);
+    launch_morton(a, s);
+    launch_seg_scan(a, s);
+    h->sorted = radix_sort_pairs(h->wide, h->keys[0].p, h->keys[1].p, reinterpret_cast<int *>(h->vals[0].p),
+                                 reinterpret_cast<int *>(h->vals[1].p), n, bits, h->sort_scratch.p,
+                                 &a.status->err, s);
+    a.keys_sorted = h->keys[h->sorted].p;
+    a.order = reinterpret_cast<const int *>(h->vals[h->sorted].p);
+    launch_karras(a, s);
+    launch_fit(a, s);
+    rc = cuda_status();
+    if (rc) return rc;
+    h->built = true;
+    return QBVH_OK;
+}
+
+int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s)
+{
+    if (!h) return QBVH_ERR_INVALID_ARG;
+    if (!h->built) return QBVH_ERR_NOT_BUILT;
+    if (!r_list_host || cap < 1) return QBVH_ERR_INVALID_ARG;
+    const int T = h->n_types;
+    if ((long long)h->n * cap >= (1LL << 40)) return QBVH_ERR_INVALID_ARG;
+    QueryArgs q;
+    memset(&q, 0, sizeof q);
+    for (int a = 0; a < T; ++a)
+        for (int b = 0; b < T; ++b) {
+            const float r = r_list_host[a * T + b];
+            if (!(r >= 0.f) || !isfinite(r) || r != r_list_host[b * T + a]) return QBVH_ERR_INVALID_ARG;
+            if (h->n > 0 && r > 0.f && !(r < 0.5f * h->L_min)) return QBVH_ERR_CUTOFF_TOO_LARGE;
+            q.r_list[a * T + b] = r;
+            q.rl2[a * T + b] = r * r;
+            // padded search radius: covers FP32 rounding of the image position
+            // and of the exact test (see query.cu), rounded up
+            const float rs = round_up_f((double)r * (1.0 + ldexp(1.0, -20)) + ldexp((double)h->L_max, -19));
+            q.rs[a * T + b] = rs;
+            q.rs2[a * T + b] = round_up_f((double)rs * (double)rs);
+        }
+    DeviceGuard g(h->device);
+    int rc = ensure(h, h->rows, (size_t)(h->n > 0 ? h->n : 1) * cap * 4);
+    rc = rc ? rc : ensure(h, h->counts, (size_t)(h->n > 0 ? h->n : 1) * 4);
+    if (rc) return rc;
+    DevStatus *st = reinterpret_cast<DevStatus *>(h->status.p);
+    if (cudaMemsetAsync(&st->max_count, 0, sizeof(int), s) != cudaSuccess) return QBVH_ERR_CUDA;
+    q.nodes = reinterpret_cast<const int4 *>(h->nodes.p);
+    q.leaves = reinterpret_cast<const float4 *>(h->leaves.p);
+    q.leaf_q = reinterpret_cast<const uint2 *>(h->leaf_q.p);
+    q.keys_sorted = h->keys[h->sorted].p;
+    q.wide_keys = h->wide;
+    q.seg = reinterpret_cast<const SegInfo *>(h->seg.p);
+    q.sys = reinterpret_cast<const SysInfo *>(h->sys.p);
+    q.n = h->n;
+    q.n_types = T;
+    q.cap = cap;
+    q.rows = reinterpret_cast<int *>(h->rows.p);
+    q.counts = reinterpret_cast<int *>(h->counts.p);
+    q.status = st;
+    q.candidates = h->candidates;
+    q.block = h->query_block;
+    launch_query(q, s);
+    if (cudaMemcpyAsync(h->h_status, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return QBVH_ERR_CUDA;
+    rc = cuda_status();
+    if (rc) return rc;
+    h->cap = cap;
+    memcpy(h->r_list, q.r_list, sizeof q.r_list);
+    h->have_list = true;
+    return QBVH_OK;
+}
+
+int status_check(qbvh_ctx *h)
+{
+    h->max_count = h->h_status->max_count;
+    int rc = map_dev_err(h->h_status->err);
+    if (h->fault == FAULT_TIMEOUT) rc = QBVH_ERR_DEVICE_TIMEOUT;
+    if (rc) return rc;
+    if (h->fault == FAULT_OVERFLOW && h->max_count <= h->cap) h->max_count = h->cap + 1;
+    if (h->max_count > h->cap) return QBVH_ERR_OVERFLOW;
+    return QBVH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *qbvh_strerror(int code)
+{
+    switch (code) {
+    case QBVH_OK: return "ok";
+    case QBVH_ERR_INVALID_ARG: return "invalid argument";
+    case QBVH_ERR_OUT_OF_BOX: return "position outside [0, L) or not finite";
+    case QBVH_ERR_BAD_TYPE: return "particle type outside [0, n_types)";
+    case QBVH_ERR_CUTOFF_TOO_LARGE: return "list radius must be below half the box edge";
+    case QBVH_ERR_OVERFLOW: return "neighbor row capacity exceeded after all retries";
+    case QBVH_ERR_DEVICE_TIMEOUT: return "bounded device-side wait gave up";
+    case QBVH_ERR_CUDA: return "CUDA runtime error";
+    case QBVH_ERR_OOM: return "out of memory";
+    case QBVH_ERR_NOT_BUILT: return "no tree or list built yet";
+    case QBVH_ERR_INTERNAL: return "device-side consistency check failed";
+    default: return "unknown status";
+    }
+}
+
+int qbvh_create(qbvh_handle *out, int device)
+{
+    if (!out) return QBVH_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return QBVH_ERR_CUDA;
+    }
+    qbvh_ctx *h = new qbvh_ctx();
+    h->device = device;
+    h->fault = read_fault_env();
+    DeviceGuard g(device);
+    if (cudaMallocHost(&h->h_status, sizeof(DevStatus)) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return QBVH_ERR_OOM;
+    }
+    memset(h->h_status, 0, sizeof(DevStatus));
+    *out = h;
+    return QBVH_OK;
+}
+
+int qbvh_destroy(qbvh_handle h)
+{
+    if (!h) return QBVH_ERR_INVALID_ARG;
+    {
+        DeviceGuard g(h->device);
+        cudaDeviceSynchronize();
+        DevBuf *all[] = {&h->keys[0], &h->keys[1], &h->vals[0], &h->vals[1], &h->sort_scratch, &h->nodes,
+                         &h->leaves, &h->leaf_q, &h->range, &h->child, &h->par_int, &h->par_leaf, &h->visit,
+                         &h->seg, &h->acc, &h->seg_start, &h->frames, &h->sys, &h->sys_off, &h->status,
+                         &h->rows, &h->counts, &h->lj_partials, &h->lj_blk_sys, &h->lj_blk_first,
+                         &h->lj_sys_blk};
+        for (DevBuf *b : all) release(*b);
+        if (h->h_status) cudaFreeHost(h->h_status);
+    }
+    delete h;
+    return QBVH_OK;
+}
+
+int qbvh_set_option(qbvh_handle h, int option, int value)
+{
+    if (!h) return QBVH_ERR_INVALID_ARG;
+    switch (option) {
+    case QBVH_OPT_BUNDLE:
+        if (value < 1 || value > 32) return QBVH_ERR_INVALID_ARG;
+        h->bundle_k = value;
+        return QBVH_OK;
+    case QBVH_OPT_QUERY_BLOCK:
+        if (value < 32 || value > 1024 || (value & 31)) return QBVH_ERR_INVALID_ARG;
+        h->query_block = value;
+        return QBVH_OK;
+    case QBVH_OPT_CANDIDATES:
+        if (value != 0 && value != 1) return QBVH_ERR_INVALID_ARG;
+        h->candidates = value;
+        return QBVH_OK;
+    default: return QBVH_ERR_INVALID_ARG;
+    }
+}
+
+int qbvh_get_option(qbvh_handle h, int option, int *value)
+{
+    if (!h || !value) return QBVH_ERR_INVALID_ARG;
+    switch (option) {
+    case QBVH_OPT_BUNDLE: *value = h->bundle_k; return QBVH_OK;
+    case QBVH_OPT_QUERY_BLOCK: *value = h->query_block; return QBVH_OK;
+    case QBVH_OPT_CANDIDATES: *value = h->candidates; return QBVH_OK;
+    default: return QBVH_ERR_INVALID_ARG;
+    }
+}
+
+int qbvh_build(qbvh_handle h, const void *pos_dev, int n, float L, int n_types, cudaStream_t stream)
+{
+    int off[2] = {0, n};
+    return build_impl(h, pos_dev, n, 1, off, &L, n_types, stream);
+}
+
+int qbvh_build_batched(qbvh_handle h, const void *pos_dev, int n_total, int n_sys, const int *sys_offsets_host,
+                       const float *L_host, int n_types, cudaStream_t stream)
+{
+    return build_impl(h, pos_dev, n_total, n_sys, sys_offsets_host, L_host, n_types, stream);
+}
+
+int qbvh_query_async(qbvh_handle h, const float *r_list_host, int cap, cudaStream_t stream)
+{
+    return query_enqueue(h, r_list_host, cap, stream);
+}
+
+int qbvh_query_status(qbvh_handle h, int *max_count)
+{
+    if (!h) return QBVH_ERR_INVALID_ARG;
+    if (!h->have_list) return QBVH_ERR_NOT_BUILT;
+    int rc = status_check(h);
+    if (max_count) *max_count = h->max_count;
+    return rc;
+}
+
+int qbvh_query(qbvh_handle h, const float *r_list_host, int cap, int max_retries, cudaStream_t stream)
+{
+    if (!h) return QBVH_ERR_INVALID_ARG;
+    if (max_retries < 0) return QBVH_ERR_INVALID_ARG;
+    for (int attempt = 0;; ++attempt) {
+        int rc = query_enqueue(h, r_list_host, cap, stream);
+        if (rc) return rc;
+        {
+            DeviceGuard g(h->device);
+            if (cudaStreamSynchronize(stream) != cudaSuccess) {
+                cudaGetLastError();
+                return QBVH_ERR_CUDA;
+            }
+        }
+        rc = status_check(h);
+        if (rc != QBVH_ERR_OVERFLOW) return rc;
+        if (attempt >= max_retries) return QBVH_ERR_OVERFLOW;
+        cap = ((h->max_count + 31) / 32) * 32;
+    }
+}
+
+int nlist_get(qbvh_handle h, const int **rows, const int **counts, int *cap, int *max_count)
+{
+    if (!h) return QBVH_ERR_INVALID_ARG;
+    if (!h->have_list) return QBVH_ERR_NOT_BUILT;
+    if (rows) *rows = reinterpret_cast<const int *>(h->rows.p);
+    if (counts) *counts = reinterpret_cast<const int *>(h->counts.p);
+    if (cap) *cap = h->cap;
+    if (max_count) *max_count = h->max_count;
+    return QBVH_OK;
+}
+
+int qbvh_tree_get(qbvh_handle h, const void **nodes, const void **leaves, const int **order, const int **seg_start,
+                  const float **frames, int *n_seg)
+{
+    if (!h) return QBVH_ERR_INVALID_ARG;
+    if (!h->built) return QBVH_ERR_NOT_BUILT;
+    if (nodes) *nodes = h->nodes.p;
+    if (leaves) *leaves = h->leaves.p;
+    if (order) *order = reinterpret_cast<const int *>(h->vals[h->sorted].p);
+    if (seg_start) *seg_start = reinterpret_cast<const int *>(h->seg_start.p);
+    if (frames) *frames = reinterpret_cast<const float *>(h->frames.p);
+    if (n_seg) *n_seg = h->n_seg;
+    return QBVH_OK;
+}
+
+int qbvh_lj_forward(qbvh_handle h, const void *pos_dev, const float *eps_dev, const float *sig_dev,
+                    const float *r_cut_host, float *e_dev, double *U_dev, float *F_dev, double *dE_dev,
+                    double *dS_dev, cudaStream_t stream)
+{
+    if (!h) return QBVH_ERR_INVALID_ARG;
+    if (!h->have_list) return QBVH_ERR_NOT_BUILT;
+    if (!eps_dev || !sig_dev || !r_cut_host || !U_dev) return QBVH_ERR_INVALID_ARG;
+    if (h->n > 0 && (!pos_dev || ((uintptr_t)pos_dev & 15u))) return QBVH_ERR_INVALID_ARG;
+    const int T = h->n_types;
+    LJArgs a;
+    memset(&a, 0, sizeof a);
+    for (int p = 0; p < T * T; ++p) {
+        const float rc = r_cut_host[p];
+        if (!(rc > 0.f) || !isfinite(rc) || rc > h->r_list[p]) return QBVH_ERR_INVALID_ARG;
+        a.rc2[p] = rc * rc;
+    }
+    DeviceGuard g(h->device);
+    // block tables: every block covers particles of one system
+    const int B = lj_block_size();
+    int rc = QBVH_OK;
+    if (h->lj_layout_off != h->off || h->lj_blk_sys.p == nullptr) {
+        std::vector<int> blk_sys, blk_first, sys_blk(h->n_sys + 1, 0);
+        for (int k = 0; k < h->n_sys; ++k) {
+            sys_blk[k] = (int)blk_sys.size();
+            for (int f = h->off[k]; f < h->off[k + 1]; f += B) {
+                blk_sys.push_back(k);
+                blk_first.push_back(f);
+            }
+        }
+        sys_blk[h->n_sys] = (int)blk_sys.size();
+        h->lj_n_blocks = (int)blk_sys.size();
+        if (blk_sys.empty()) {
+            blk_sys.push_back(0);
+            blk_first.push_back(0);
+        }
+        rc = rc ? rc : ensure(h, h->lj_blk_sys, blk_sys.size() * 4);
+        rc = rc ? rc : ensure(h, h->lj_blk_first, blk_first.size() * 4);
+        rc = rc ? rc : ensure(h, h->lj_sys_blk, sys_blk.size() * 4);
+        if (rc) return rc;
+        if (cudaMemcpyAsync(h->lj_blk_sys.p, blk_sys.data(), blk_sys.size() * 4, cudaMemcpyHostToDevice, stream) ||
+            cudaMemcpyAsync(h->lj_blk_first.p, blk_first.data(), blk_first.size() * 4, cudaMemcpyHostToDevice,
+                            stream) ||
+            cudaMemcpyAsync(h->lj_sys_blk.p, sys_blk.data(), sys_blk.size() * 4, cudaMemcpyHostToDevice, stream))
+            return QBVH_ERR_CUDA;
+        h->lj_layout_off = h->off;
+    }
+    const int np = 1 + 2 * T * T;
+    rc = ensure(h, h->lj_partials, (size_t)(h->lj_n_blocks > 0 ? h->lj_n_blocks : 1) * np * 8);
+    if (rc) return rc;
+    a.pos = reinterpret_cast<const float4 *>(pos_dev);
+    a.rows = reinterpret_cast<const int *>(h->rows.p);
+    a.counts = reinterpret_cast<const int *>(h->counts.p);
+    a.cap = h->cap;
+    a.n = h->n;
+    a.n_types = T;
+    a.n_sys = h->n_sys;
+    a.sys = reinterpret_cast<const SysInfo *>(h->sys.p);
+    a.blk_sys = reinterpret_cast<const int *>(h->lj_blk_sys.p);
+    a.blk_first = reinterpret_cast<const int *>(h->lj_blk_first.p);
+    a.n_blocks = h->lj_n_blocks;
+    a.eps = eps_dev;
+    a.sig = sig_dev;
+    a.e = e_dev;
+    a.F = F_dev;
+    a.partials = reinterpret_cast<double *>(h->lj_partials.p);
+    a.U = U_dev;
+    a.dE = dE_dev;
+    a.dS = dS_dev;
+    a.sys_blk_start = reinterpret_cast<const int *>(h->lj_sys_blk.p);
+    launch_lj_forward(a, stream);
+    return cuda_status();
+}
+
+int qbvh_lj_backward(qbvh_handle h, const double *g_dev, const float *F_dev, const double *dE_dev,
+                     const double *dS_dev, float *grad_pos_dev, float *grad_eps_dev, float *grad_sig_dev,
+                     cudaStream_t stream)
+{
+    if (!h) return QBVH_ERR_INVALID_ARG;
+    if (!h->built) return QBVH_ERR_NOT_BUILT;
+    if (!g_dev) return QBVH_ERR_INVALID_ARG;
+    if (grad_pos_dev && !F_dev) return QBVH_ERR_INVALID_ARG;
+    if (grad_eps_dev && !dE_dev) return QBVH_ERR_INVALID_ARG;
+    if (grad_sig_dev && !dS_dev) return QBVH_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    launch_lj_backward(g_dev, F_dev, dE_dev, dS_dev, grad_pos_dev, grad_eps_dev, grad_sig_dev, h->n, h->n_sys,
+                       h->n_types, reinterpret_cast<const SysInfo *>(h->sys.p),
+                       reinterpret_cast<const int *>(h->sys_off.p), stream);
+    return cuda_status();
+}
+
+int qbvh_pack_positions(const float *xyz_dev, const int *types_dev, int n, void *pos4_dev, cudaStream_t stream)
+{
+    if (n < 0) return QBVH_ERR_INVALID_ARG;
+    if (n > 0 && (!xyz_dev || !pos4_dev || ((uintptr_t)pos4_dev & 15u))) return QBVH_ERR_INVALID_ARG;
+    launch_pack(xyz_dev, types_dev, n, reinterpret_cast<float4 *>(pos4_dev), stream);
+    return cuda_status();
+}
+
+}  // extern "C"

@@ -1,0 +1,460 @@
+// Build of the quantized LBVH (Sec. 2.1, Sec. 2.2, Fig. 3 of the paper).
+//
+//   prepare  : reset per-tree accumulators and the device status word
+//   morton   : Morton binning of every particle (2^10 - 1 bins per axis, 30-bit
+//              code, Sec. 2.1), per-tree particle count and root AABB
+//   seg_scan : tree start offsets and quantization frames (root AABB split
+//              into 2^10 - 1 bins per axis, bin width rounded up, Sec. 2.2)
+//   (radix sort of the codes: sort.cu)
+//   karras   : binary radix tree of the sorted codes (Karras's construction,
+//              cited in Sec. 2.1): N-1 internal nodes with two children each
+//   fit      : bottom-up walk from the leaves (Sec. 2.1); each internal node
+//              is completed by the second child to arrive
+//
+// Quantization is done in the fit, in the integer domain: a leaf's bounds are
+// snapped outward onto the bin edges (lower bound rounded down, upper bound
+// up, IEEE directed rounding, Sec. 3) and an internal node's quantized bounds
+// are the per-axis min / max of its children's.  Outward snapping is monotone,
+// so the min of snapped children equals the snapped min of the children: this
+// is the quantization of the node's FP32 AABB (Sec. 2.2) without ever storing
+// the FP32 boxes.
+#include <float.h>
+
+#include "qbvh_internal.cuh"
+
+namespace qbvh {
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kLocalSegs = 64;
+
+__device__ __forceinline__ unsigned spread10(unsigned v)
+{
+    // place bit k of a 10-bit value at bit 3k
+    v &= 0x3FFu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__device__ __forceinline__ unsigned bin_of(float x, float scale)
+{
+    int b = (int)__fmul_rn(x, scale);   // truncation == floor for x >= 0
+    b = b < 0 ? 0 : b;
+    b = b > QBVH_QMAX - 1 ? QBVH_QMAX - 1 : b;
+    return (unsigned)b;
+}
+
+__device__ __forceinline__ int sys_of(const int *off, int n_sys, int i)
+{
+    // largest k with off[k] <= i
+    int lo = 0, hi = n_sys - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Per-tree accumulator layout (8 words): [0] count, [1..3] min bits of x,y,z,
+// [4..6] max bits, [7] unused.  Valid positions are >= 0, where the order of
+// IEEE floats equals the order of their bit patterns as unsigned integers.
+__device__ __forceinline__ unsigned acc_init(int f) { return (f >= 1 && f <= 3) ? 0x7F800000u : 0u; }
+
+__global__ void prepare_kernel(unsigned *acc, int n_seg, DevStatus *status)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_seg * 8) acc[t] = acc_init(t & 7);
+    if (t == 0) {
+        status->max_count = 0;
+        status->err = 0u;
+    }
+}
+
+template <bool WIDE>
+__global__ void __launch_bounds__(kBlock) morton_kernel(const BuildArgs a, unsigned *acc)
+{
+    __shared__ unsigned s_acc[kLocalSegs * 8];
+    __shared__ int s_seg0, s_span;
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    const int T = a.n_types;
+    if (threadIdx.x == 0) {
+        int first = blockIdx.x * kBlock;
+        int last = min(first + kBlock, a.n) - 1;
+        int k0 = a.n_sys > 1 ? sys_of(a.sys_off, a.n_sys, first) : 0;
+        int k1 = a.n_sys > 1 ? sys_of(a.sys_off, a.n_sys, last) : 0;
+        s_seg0 = k0 * T;
+        s_span = (k1 - k0 + 1) * T;
+    }
+    for (int t = threadIdx.x; t < kLocalSegs * 8; t += kBlock) s_acc[t] = acc_init(t & 7);
+    __syncthreads();
+    const bool local = s_span <= kLocalSegs;
+
+    unsigned err = 0u;
+    int seg = -1;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < a.n) {
+        const int k = a.n_sys > 1 ? sys_of(a.sys_off, a.n_sys, i) : 0;
+        const SysInfo sy = a.sys[k];
+        p = __ldg(a.pos + i);
+        int type = __float_as_int(p.w);
+        if (type < 0 || type >= T) {
+            err |= QBVH_DEVERR_BAD_TYPE;
+            type = type < 0 ? 0 : T - 1;
+        }
+        if (!(p.x >= 0.f && p.x < sy.L && p.y >= 0.f && p.y < sy.L && p.z >= 0.f && p.z < sy.L)) {
+            err |= QBVH_DEVERR_OUT_OF_BOX;
+            // keep the accumulators in the non-negative range; the build is
+            // reported as failed at the next query
+            p.x = fmaxf(p.x, 0.f);
+            p.y = fmaxf(p.y, 0.f);
+            p.z = fmaxf(p.z, 0.f);
+            if (!(p.x == p.x)) p.x = 0.f;
+            if (!(p.y == p.y)) p.y = 0.f;
+            if (!(p.z == p.z)) p.z = 0.f;
+        }
+        const unsigned code = (spread10(bin_of(p.x, sy.mscale)) << 2) |
+                              (spread10(bin_of(p.y, sy.mscale)) << 1) |
+                              spread10(bin_of(p.z, sy.mscale));
+        seg = k * T + type;
+        if (WIDE)
+            reinterpret_cast<unsigned long long *>(a.keys)[i] =
+                ((unsigned long long)seg << 30) | code;
+        else
+            reinterpret_cast<unsigned *>(a.keys)[i] = ((unsigned)type << 30) | code;
+    }
+    if (err) atomicOr(&a.status->err, err);
+
+    // per-tree count and root AABB: warp-aggregate when the warp is uniform
+    const unsigned full = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const int seg0 = __shfl_sync(full, seg, 0);
+    const bool uniform = __all_sync(full, seg == seg0) && seg0 >= 0;
+    unsigned v[7];
+    v[0] = 1u;
+    v[1] = __float_as_uint(p.x);
+    v[2] = __float_as_uint(p.y);
+    v[3] = __float_as_uint(p.z);
+    v[4] = v[1];
+    v[5] = v[2];
+    v[6] = v[3];
+    unsigned *dst_base = nullptr;
+    if (uniform) {
+        v[0] = __reduce_add_sync(full, 1u);
+        for (int f = 1; f <= 3; ++f) v[f] = __reduce_min_sync(full, v[f]);
+        for (int f = 4; f <= 6; ++f) v[f] = __reduce_max_sync(full, v[f]);
+        if (lane == 0) {
+            dst_base = local ? s_acc + (seg0 - s_seg0) * 8 : acc + (size_t)seg0 * 8;
+        }
+    } else if (seg >= 0) {
+        dst_base = local ? s_acc + (seg - s_seg0) * 8 : acc + (size_t)seg * 8;
+    }
+    if (dst_base) {
+        atomicAdd(dst_base, v[0]);
+        for (int f = 1; f <= 3; ++f) atomicMin(dst_base + f, v[f]);
+        for (int f = 4; f <= 6; ++f) atomicMax(dst_base + f, v[f]);
+    }
+    if (local) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < s_span * 8; t += kBlock) {
+            const int f = t & 7;
+            const unsigned x = s_acc[t];
+            const unsigned cnt = s_acc[t & ~7];
+            if (cnt == 0u || f == 7) continue;
+            unsigned *g = acc + (size_t)s_seg0 * 8 + t;
+            if (f == 0) atomicAdd(g, x);
+            else if (f <= 3) atomicMin(g, x);
+            else atomicMax(g, x);
+        }
+    }
+}
+
+// One block: exclusive scan of the tree counts, tree records and frames.
+__global__ void __launch_bounds__(1024) seg_scan_kernel(const BuildArgs a, const unsigned *acc)
+{
+    __shared__ int s_warp[32];
+    __shared__ int s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < a.n_seg; base += 1024) {
+        const int s = base + tid;
+        const int c = s < a.n_seg ? (int)acc[(size_t)s * 8] : 0;
+        int x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = s_warp[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+                if (lane >= o) w += y;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const int incl = x + (warp > 0 ? s_warp[warp - 1] : 0) + s_carry;
+        const int start = incl - c;
+        if (s < a.n_seg) {
+            SegInfo g;
+            g.start = start;
+            g.count = c;
+            g.sys = s / a.n_types;
+            g.type = s % a.n_types;
+            g.pad = 0.f;
+            float *fr = a.frames + (size_t)s * 8;
+            for (int d = 0; d < 3; ++d) {
+                float lo = __uint_as_float(acc[(size_t)s * 8 + 1 + d]);
+                float hi = __uint_as_float(acc[(size_t)s * 8 + 4 + d]);
+                if (c == 0) lo = hi = 0.f;
+                // bin width: (R_hi - R_lo) / 1023 rounded up, so 1023 bins cover the root
+                float h = __fdiv_ru(__fsub_ru(hi, lo), (float)QBVH_QMAX);
+                if (!(h >= FLT_MIN)) h = FLT_MIN;
+                g.rlo[d] = lo;
+                g.rhi[d] = hi;
+                g.h[d] = h;
+                fr[d] = lo;
+                fr[3 + d] = h;
+            }
+            fr[6] = 0.f;
+            fr[7] = 0.f;
+            a.seg[s] = g;
+            a.seg_start[s] = start;
+            if (s == a.n_seg - 1) a.seg_start[a.n_seg] = incl;
+        }
+        __syncthreads();
+        if (tid == 1023) s_carry = incl;
+        __syncthreads();
+    }
+}
+
+template <bool WIDE>
+__device__ __forceinline__ unsigned long long key_at(const void *keys, int k)
+{
+    if (WIDE) return __ldg(reinterpret_cast<const unsigned long long *>(keys) + k);
+    return __ldg(reinterpret_cast<const unsigned *>(keys) + k);
+}
+
+template <bool WIDE>
+__device__ __forceinline__ int seg_of_key(unsigned long long key, int n_types)
+{
+    if (WIDE) return (int)(key >> 30);
+    return n_types > 1 ? (int)(key >> 30) : 0;
+}
+
+// Length of the common prefix of the augmented keys (code, sorted position)
+// of leaves i and j inside [a, b]; -1 outside.
+template <bool WIDE>
+__device__ __forceinline__ int delta(const void *keys, int i, unsigned ci, int j, int a, int b)
+{
+    if (j < a || j > b) return -1;
+    const unsigned cj = (unsigned)key_at<WIDE>(keys, j) & QBVH_QMASK;
+    if (ci != cj) return __clz(ci ^ cj);
+    return 32 + __clz((unsigned)i ^ (unsigned)j);
+}
+
+template <bool WIDE>
+__global__ void __launch_bounds__(kBlock) karras_kernel(const BuildArgs a)
+{
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= a.n) return;
+    const unsigned long long key = key_at<WIDE>(a.keys_sorted, i);
+    const int s = seg_of_key<WIDE>(key, a.n_types);
+    const SegInfo g = a.seg[s];
+    const int lo = g.start, hi = g.start + g.count - 1;
+    if (i == hi) {
+        if (g.count == 1) a.par_leaf[i] = -1;
+        return;   // no internal node at a tree's last leaf
+    }
+    const unsigned ci = (unsigned)key & QBVH_QMASK;
+    const void *K = a.keys_sorted;
+    // direction of the range
+    const int d = (delta<WIDE>(K, i, ci, i + 1, lo, hi) - delta<WIDE>(K, i, ci, i - 1, lo, hi)) > 0 ? 1 : -1;
+    const int dmin = delta<WIDE>(K, i, ci, i - d, lo, hi);
+    // upper bound on the range length, then binary search for the other end
+    int lmax = 2;
+    while (delta<WIDE>(K, i, ci, i + lmax * d, lo, hi) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta<WIDE>(K, i, ci, i + (l + t) * d, lo, hi) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = delta<WIDE>(K, i, ci, j, lo, hi);
+    // binary search for the split position
+    int sp = 0;
+    int t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta<WIDE>(K, i, ci, i + (sp + t) * d, lo, hi) > dnode) sp += t;
+    } while (t > 1);
+    const int gamma = i + sp * d + min(d, 0);
+    const int first = min(i, j), last = max(i, j);
+    const int left = (first == gamma) ? ~gamma : gamma;
+    const int right = (last == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+    a.range[i] = make_int2(first, last);
+    a.child[i] = make_int2(left, right);
+    if (left >= 0) a.par_int[left] = i; else a.par_leaf[~left] = i;
+    if (right >= 0) a.par_int[right] = i; else a.par_leaf[~right] = i;
+    if (i == lo) a.par_int[i] = -1;   // node lo of a tree is its root
+}
+
+__device__ __forceinline__ unsigned pack3(unsigned x, unsigned y, unsigned z)
+{
+    return (x << 20) | (y << 10) | z;
+}
+
+__device__ __forceinline__ unsigned qmin3(unsigned a, unsigned b)
+{
+    return pack3(min((a >> 20) & 1023u, (b >> 20) & 1023u), min((a >> 10) & 1023u, (b >> 10) & 1023u),
+                 min(a & 1023u, b & 1023u));
+}
+
+__device__ __forceinline__ unsigned qmax3(unsigned a, unsigned b)
+{
+    return pack3(max((a >> 20) & 1023u, (b >> 20) & 1023u), max((a >> 10) & 1023u, (b >> 10) & 1023u),
+                 max(a & 1023u, b & 1023u));
+}
+
+// Lower bound snapped down / upper bound snapped up onto the bin edges.
+__device__ __forceinline__ unsigned q_down(float x, float r, float h)
+{
+    float v = floorf(__fdiv_rd(__fsub_rd(x, r), h));
+    v = fminf(fmaxf(v, 0.f), (float)QBVH_QMAX);
+    return (unsigned)v;
+}
+
+__device__ __forceinline__ unsigned q_up(float x, float r, float h)
+{
+    float v = ceilf(__fdiv_ru(__fsub_ru(x, r), h));
+    v = fminf(fmaxf(v, 0.f), (float)QBVH_QMAX);
+    return (unsigned)v;
+}
+
+// Rope of the subtree whose leaves end at `last` in tree [lo, hi]: the node
+// visited next in pre-order is the shallowest node starting at last + 1.  That
+// node is a right child, and a right child's Karras index is its first leaf,
+// so it is internal node last+1 if that node starts at last+1, else leaf last+1.
+__device__ __forceinline__ int rope_after(const int2 *range, int last, int hi)
+{
+    const int k = last + 1;
+    if (k > hi) return QBVH_END;
+    if (k <= hi - 1 && range[k].x == k) return k;
+    return ~k;
+}
+
+template <bool WIDE>
+__global__ void __launch_bounds__(kBlock) fit_kernel(const BuildArgs a)
+{
+    const int k = blockIdx.x * kBlock + threadIdx.x;
+    if (k >= a.n) return;
+    const unsigned long long key = key_at<WIDE>(a.keys_sorted, k);
+    const int s = seg_of_key<WIDE>(key, a.n_types);
+    const SegInfo g = a.seg[s];
+    const int hi = g.start + g.count - 1;
+
+    int orig = __ldg(a.order + k);
+    if ((unsigned)orig >= (unsigned)a.n) {
+        atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
+        orig = 0;
+    }
+    const float4 p = __ldg(a.pos + orig);
+    const int rope = rope_after(a.range, k, hi);
+    const unsigned tag = (unsigned)orig | ((rope >= 0 ? 1u : 0u) << 31);
+    a.leaves[k] = make_float4(p.x, p.y, p.z, __uint_as_float(tag));
+
+    uint2 q;
+    q.x = pack3(q_down(p.x, g.rlo[0], g.h[0]), q_down(p.y, g.rlo[1], g.h[1]), q_down(p.z, g.rlo[2], g.h[2]));
+    q.y = pack3(q_up(p.x, g.rlo[0], g.h[0]), q_up(p.y, g.rlo[1], g.h[1]), q_up(p.z, g.rlo[2], g.h[2]));
+    a.leaf_q[k] = q;
+
+    int node = a.par_leaf[k];
+    // a radix tree over 62-bit keys (30-bit code + 32-bit position) is at most
+    // 63 levels deep; a longer walk means a broken parent link
+    for (int depth = 0; node >= 0; ++depth) {
+        if (node >= a.n || depth > 64) {
+            atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
+            return;
+        }
+        __threadfence();   // publish this child's bounds before arriving
+        if (atomicAdd(a.visit + node, 1) == 0) return;   // sibling not done yet
+        const int2 c = a.child[node];
+        if (c.x >= a.n || ~c.x >= a.n || c.y >= a.n || ~c.y >= a.n) {
+            atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
+            return;
+        }
+        uint2 bl, br;
+        if (c.x >= 0) {
+            int4 w = __ldcg(a.nodes + c.x);
+            bl = make_uint2((unsigned)w.x & QBVH_QMASK, (unsigned)w.y);
+        } else {
+            bl = __ldcg(a.leaf_q + ~c.x);
+        }
+        if (c.y >= 0) {
+            int4 w = __ldcg(a.nodes + c.y);
+            br = make_uint2((unsigned)w.x & QBVH_QMASK, (unsigned)w.y);
+        } else {
+            br = __ldcg(a.leaf_q + ~c.y);
+        }
+        const unsigned qlo = qmin3(bl.x, br.x);
+        const unsigned qhi = qmax3(bl.y, br.y);
+        const int2 r = a.range[node];
+        const int count = r.y - r.x + 1;
+        const int bundle = (a.bundle_k >= 2 && count <= a.bundle_k) ? 1 : 0;
+        int4 w;
+        w.x = (int)(qlo | ((unsigned)bundle << 31));
+        w.y = (int)qhi;
+        w.z = bundle ? r.x : c.x;
+        w.w = rope_after(a.range, r.y, hi);
+        __stcg(a.nodes + node, w);
+        node = a.par_int[node];
+    }
+}
+
+inline int blocks_for(int n, int b) { return (n + b - 1) / b; }
+
+}  // namespace
+
+void launch_build_prepare(const BuildArgs &a, cudaStream_t s)
+{
+    const int work = a.n_seg * 8 > 1 ? a.n_seg * 8 : 1;
+    prepare_kernel<<<blocks_for(work, kBlock), kBlock, 0, s>>>(a.seg_rootbits, a.n_seg, a.status);
+}
+
+void launch_morton(const BuildArgs &a, cudaStream_t s)
+{
+    if (a.n == 0) return;
+    if (a.wide_keys)
+        morton_kernel<true><<<blocks_for(a.n, kBlock), kBlock, 0, s>>>(a, a.seg_rootbits);
+    else
+        morton_kernel<false><<<blocks_for(a.n, kBlock), kBlock, 0, s>>>(a, a.seg_rootbits);
+}
+
+void launch_seg_scan(const BuildArgs &a, cudaStream_t s)
+{
+    seg_scan_kernel<<<1, 1024, 0, s>>>(a, a.seg_rootbits);
+}
+
+void launch_karras(const BuildArgs &a, cudaStream_t s)
+{
+    if (a.n == 0) return;
+    if (a.wide_keys)
+        karras_kernel<true><<<blocks_for(a.n, kBlock), kBlock, 0, s>>>(a);
+    else
+        karras_kernel<false><<<blocks_for(a.n, kBlock), kBlock, 0, s>>>(a);
+}
+
+void launch_fit(const BuildArgs &a, cudaStream_t s)
+{
+    if (a.n == 0) return;
+    if (a.wide_keys)
+        fit_kernel<true><<<blocks_for(a.n, kBlock), kBlock, 0, s>>>(a);
+    else
+        fit_kernel<false><<<blocks_for(a.n, kBlock), kBlock, 0, s>>>(a);
+}
+
+}  // namespace qbvh

@@ -1,0 +1,226 @@
+// Truncated-and-shifted Lennard-Jones energy over a neighbor list (Eq. 1 of
+// the paper, shifted to zero at r_c as described in Sec. 1), in one fused pass
+// that also produces the forces and the gradients with respect to the
+// per-type-pair parameters:
+//
+//   s = (sig / r)^6,  s_c = (sig / r_c)^6
+//   u(r)          = 4 eps (s^2 - s) - 4 eps (s_c^2 - s_c)           (r < r_c)
+//   e_i           = 1/2 sum_{j in N(i)} u(r_ij)          (full list: each pair twice)
+//   F_i           = sum_j 24 eps (2 s^2 - s) / r^2 (x_i - x_j)
+//   dU/deps[a][b] = 1/2 sum_{i:a, j:b} u / eps
+//   dU/dsig[a][b] = 1/2 sum_{i:a, j:b} (24 eps / sig) [(2 s^2 - s) - (2 s_c^2 - s_c)]
+//
+// Per-particle sums are FP32 in registers.  Each block covers particles of a
+// single system and reduces its FP32 contributions in FP64 into one partial
+// record; a second kernel adds the records of each system in a fixed order,
+// so the FP64 totals are deterministic.
+#include "qbvh_internal.cuh"
+
+namespace qbvh {
+
+namespace {
+
+constexpr int kLJBlock = 128;
+
+__device__ __forceinline__ float mi_component(float d, float L, float Linv)
+{
+    return __fsub_rn(d, __fmul_rn(L, rintf(__fmul_rn(d, Linv))));
+}
+
+template <int T>
+__global__ void __launch_bounds__(kLJBlock) lj_forward_kernel(const __grid_constant__ LJArgs a)
+{
+    constexpr int NP = 1 + 2 * T * T;
+    __shared__ float s_eps[T * T], s_sig[T * T], s_sig2[T * T], s_phic[T * T], s_dsc[T * T], s_rc2[T * T];
+    __shared__ double s_red[kLJBlock / 32][NP];
+    const int tid = threadIdx.x;
+    if (tid < T * T) {
+        const float e = a.eps[tid], sg = a.sig[tid];
+        s_eps[tid] = e;
+        s_sig[tid] = sg;
+        s_sig2[tid] = sg * sg;
+        s_rc2[tid] = a.rc2[tid];
+        const float sc2 = (sg * sg) / a.rc2[tid];
+        const float sc6 = sc2 * sc2 * sc2;
+        s_phic[tid] = 4.f * (sc6 * sc6 - sc6);   // shift per unit eps
+        s_dsc[tid] = 2.f * sc6 * sc6 - sc6;
+    }
+    __syncthreads();
+    const int sys = a.blk_sys[blockIdx.x];
+    const SysInfo sy = a.sys[sys];
+    const int i = a.blk_first[blockIdx.x] + tid;
+    const bool active = i < sy.offset + sy.count;
+    float e = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+    float gE[T], gS[T];
+#pragma unroll
+    for (int b = 0; b < T; ++b) gE[b] = gS[b] = 0.f;
+    int ta = 0;
+    if (active) {
+        const float4 pi = __ldg(a.pos + i);
+        ta = T > 1 ? __float_as_int(pi.w) : 0;
+        ta = ta < 0 ? 0 : (ta >= T ? T - 1 : ta);
+        const int c = min(__ldg(a.counts + i), a.cap);
+        const int *row = a.rows + (size_t)i * a.cap;
+        for (int k = 0; k < c; ++k) {
+            const int j = __ldg(row + k);
+            if ((unsigned)j >= (unsigned)a.n) continue;   // never for a list from the traversal
+            const float4 pj = __ldg(a.pos + j);
+            int tb = T > 1 ? __float_as_int(pj.w) : 0;
+            tb = tb < 0 ? 0 : (tb >= T ? T - 1 : tb);
+            const int p = ta * T + tb;
+            const float dx = mi_component(__fsub_rn(pj.x, pi.x), sy.L, sy.Linv);
+            const float dy = mi_component(__fsub_rn(pj.y, pi.y), sy.L, sy.Linv);
+            const float dz = mi_component(__fsub_rn(pj.z, pi.z), sy.L, sy.Linv);
+            const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+            if (!(r2 < s_rc2[p])) continue;
+            const float s2 = s_sig2[p] / r2;
+            const float s6 = s2 * s2 * s2;
+            const float uE = 4.f * (s6 * s6 - s6) - s_phic[p];   // u / eps
+            const float q = 2.f * s6 * s6 - s6;
+            const float w = 24.f * s_eps[p] * q / r2;
+            e += s_eps[p] * uE;
+            fx -= w * dx;
+            fy -= w * dy;
+            fz -= w * dz;
+#pragma unroll
+            for (int b = 0; b < T; ++b) {
+                if (b == tb) {
+                    gE[b] += uE;
+                    gS[b] += (24.f * s_eps[p] / s_sig[p]) * (q - s_dsc[p]);
+                }
+            }
+        }
+        e *= 0.5f;
+        if (a.e) a.e[i] = e;
+        if (a.F) {
+            a.F[3 * (size_t)i] = fx;
+            a.F[3 * (size_t)i + 1] = fy;
+            a.F[3 * (size_t)i + 2] = fz;
+        }
+    }
+    // FP64 block reduction of energy and the parameter-gradient contributions
+    double v[NP];
+    v[0] = (double)e;
+#pragma unroll
+    for (int q = 1; q < NP; ++q) v[q] = 0.0;
+    if (active) {
+#pragma unroll
+        for (int b = 0; b < T; ++b) {
+            v[1 + ta * T + b] = 0.5 * (double)gE[b];
+            v[1 + T * T + ta * T + b] = 0.5 * (double)gS[b];
+        }
+    }
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        double x = v[q];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+        if (lane == 0) s_red[warp][q] = x;
+    }
+    __syncthreads();
+    for (int q = tid; q < NP; q += kLJBlock) {
+        double x = 0.0;
+        for (int w = 0; w < kLJBlock / 32; ++w) x += s_red[w][q];
+        a.partials[(size_t)blockIdx.x * NP + q] = x;
+    }
+}
+
+// One block per system: fixed-order FP64 sum of the block records.
+__global__ void lj_finalize_kernel(const double *partials, const int *sys_blk_start, int np, int T, double *U,
+                                   double *dE, double *dS)
+{
+    __shared__ double s[256];
+    const int sys = blockIdx.x;
+    const int b0 = sys_blk_start[sys], b1 = sys_blk_start[sys + 1];
+    for (int q = 0; q < np; ++q) {
+        double x = 0.0;
+        for (int b = b0 + (int)threadIdx.x; b < b1; b += blockDim.x) x += partials[(size_t)b * np + q];
+        s[threadIdx.x] = x;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double tot = s[0];
+            if (q == 0) U[sys] = tot;
+            else if (q <= T * T) { if (dE) dE[(size_t)sys * T * T + (q - 1)] = tot; }
+            else if (dS) dS[(size_t)sys * T * T + (q - 1 - T * T)] = tot;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void lj_backward_pos_kernel(const double *g, const float *F, float *gpos, int n, int n_sys,
+                                       const int *sys_off)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = n_sys - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(sys_off + mid) <= i) lo = mid; else hi = mid - 1;
+    }
+    const float gs = (float)g[lo];
+    for (int d = 0; d < 3; ++d) gpos[3 * (size_t)i + d] = -gs * F[3 * (size_t)i + d];
+}
+
+__global__ void lj_backward_param_kernel(const double *g, const double *dE, const double *dS, float *geps,
+                                         float *gsig, int n_sys, int TT)
+{
+    const int q = threadIdx.x;
+    if (q >= TT) return;
+    double xe = 0.0, xs = 0.0;
+    for (int k = 0; k < n_sys; ++k) {
+        if (dE) xe += g[k] * dE[(size_t)k * TT + q];
+        if (dS) xs += g[k] * dS[(size_t)k * TT + q];
+    }
+    if (geps) geps[q] = (float)xe;
+    if (gsig) gsig[q] = (float)xs;
+}
+
+__global__ void pack_kernel(const float *xyz, const int *types, int n, float4 *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int t = types ? types[i] : 0;
+    out[i] = make_float4(xyz[3 * (size_t)i], xyz[3 * (size_t)i + 1], xyz[3 * (size_t)i + 2], __int_as_float(t));
+}
+
+}  // namespace
+
+int lj_block_size() { return kLJBlock; }
+
+void launch_lj_forward(const LJArgs &a, cudaStream_t s)
+{
+    if (a.n_blocks > 0) {
+        switch (a.n_types) {
+        case 1: lj_forward_kernel<1><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
+        case 2: lj_forward_kernel<2><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
+        case 3: lj_forward_kernel<3><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
+        case 4: lj_forward_kernel<4><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
+        case 5: lj_forward_kernel<5><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
+        case 6: lj_forward_kernel<6><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
+        case 7: lj_forward_kernel<7><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
+        default: lj_forward_kernel<8><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
+        }
+    }
+    const int T = a.n_types;
+    lj_finalize_kernel<<<a.n_sys, 256, 0, s>>>(a.partials, a.sys_blk_start, 1 + 2 * T * T, T, a.U, a.dE, a.dS);
+}
+
+void launch_lj_backward(const double *g, const float *F, const double *dE, const double *dS, float *gpos,
+                        float *geps, float *gsig, int n, int n_sys, int n_types, const SysInfo *sys,
+                        const int *sys_off, cudaStream_t s)
+{
+    (void)sys;
+    if (gpos && F && n > 0) lj_backward_pos_kernel<<<(n + 255) / 256, 256, 0, s>>>(g, F, gpos, n, n_sys, sys_off);
+    if (geps || gsig) lj_backward_param_kernel<<<1, 64, 0, s>>>(g, dE, dS, geps, gsig, n_sys, n_types * n_types);
+}
+
+void launch_pack(const float *xyz, const int *types, int n, float4 *out, cudaStream_t s)
+{
+    if (n > 0) pack_kernel<<<(n + 255) / 256, 256, 0, s>>>(xyz, types, n, out);
+}
+
+}  // namespace qbvh

@@ -1,0 +1,172 @@
+// Internal declarations shared by the qbvh CUDA translation units.
+//
+// Data layout in device memory (all arrays indexed by sorted position k unless
+// said otherwise; trees are "segments" of the sorted order, one per
+// (system, type)):
+//   keys     u32 {type<<30 | morton} or u64 {segment<<30 | morton}
+//   order    int32 sorted position -> original index (radix-sort values)
+//   range    int2  leaf range [first, last] of internal node k
+//   child    int2  {left id, right id} of internal node k
+//   par_int  int32 parent of internal node k (-1 at a root)
+//   par_leaf int32 parent of leaf k (-1 for a one-particle tree)
+//   visit    int32 arrival counter of internal node k (bottom-up fit)
+//   leaf_q   uint2 quantized AABB {lo, hi} of leaf k
+//   nodes    int4  {lo | bundle<<31, hi, left or first leaf, rope}   (Fig. 3b)
+//   leaves   float4 {x, y, z, original index | rope-is-internal<<31}
+// Node ids: k >= 0 internal node k, ~k (negative) leaf k, QBVH_END = INT32_MIN.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define QBVH_END ((int)0x80000000)
+
+// device error word bits
+#define QBVH_DEVERR_OUT_OF_BOX 1u
+#define QBVH_DEVERR_BAD_TYPE 2u
+#define QBVH_DEVERR_TIMEOUT 4u
+#define QBVH_DEVERR_INTERNAL 8u
+
+// quantization: 2^10 - 1 bins per axis, bounds on the 1024 bin edges 0..1023
+#define QBVH_QMAX 1023
+#define QBVH_QMASK 0x3FFFFFFFu
+
+namespace qbvh {
+
+// Per-segment (tree) information, written by the build.
+struct SegInfo {
+    int start;      // first sorted position
+    int count;      // particles in the tree
+    int sys;        // system index
+    int type;       // particle type
+    float rlo[3];   // root AABB lower corner (fitted, exact min over positions)
+    float rhi[3];   // root AABB upper corner
+    float h[3];     // bin width per axis, rounded up, >= FLT_MIN
+    float pad;
+};
+
+// Per-system information.
+struct SysInfo {
+    int offset;     // first original index
+    int count;
+    float L;        // box edge
+    float Linv;     // fl(1 / L), computed once on the host
+    float mscale;   // fl(1023 / L): Morton bins per unit length
+    float pad[3];
+};
+
+struct DevStatus {
+    int max_count;
+    unsigned err;
+};
+
+// ---- launchers (build.cu) ------------------------------------------------
+struct BuildArgs {
+    const float4 *pos;   // [n] original order
+    int n;
+    int n_sys;
+    int n_types;
+    int n_seg;
+    bool wide_keys;      // u64 keys
+    int bundle_k;
+    const SysInfo *sys;  // [n_sys]
+    const int *sys_off;  // [n_sys + 1]
+    SegInfo *seg;        // [n_seg]
+    unsigned *seg_rootbits; // [n_seg * 8] per-tree count and root AABB accumulators
+    int *seg_start;      // [n_seg + 1]
+    float *frames;       // [n_seg * 8]
+    void *keys;          // morton keys, input of the sort
+    const void *keys_sorted;
+    const int *order;    // sorted values
+    int2 *range;
+    int2 *child;
+    int *par_int;
+    int *par_leaf;
+    int *visit;
+    uint2 *leaf_q;
+    int4 *nodes;
+    float4 *leaves;
+    DevStatus *status;
+};
+
+void launch_build_prepare(const BuildArgs &a, cudaStream_t s);
+void launch_morton(const BuildArgs &a, cudaStream_t s);
+void launch_seg_scan(const BuildArgs &a, cudaStream_t s);
+void launch_karras(const BuildArgs &a, cudaStream_t s);
+void launch_fit(const BuildArgs &a, cudaStream_t s);
+
+// ---- radix sort (sort.cu) ------------------------------------------------
+struct SortScratch {
+    unsigned *hist;        // [passes][256] digit counts -> exclusive offsets
+    unsigned *status;      // [passes][tiles][256] look-back words
+    unsigned *counters;    // [passes] tile tickets
+};
+
+size_t sort_tile_items();
+int sort_num_tiles(int n);
+size_t sort_scratch_bytes(int n, int passes);
+// Sorts (key, value) pairs stably by the low `bits` bits of the key.  keys_a
+// holds the input keys; values start as 0..n-1.  Returns the index (0 or 1)
+// of the buffer pair holding the result: 0 -> (keys_a, vals_a), 1 -> (keys_b, vals_b).
+int radix_sort_pairs(bool wide, void *keys_a, void *keys_b, int *vals_a, int *vals_b, int n,
+                     int bits, void *scratch, unsigned *err, cudaStream_t s);
+
+// ---- traversal (query.cu) ------------------------------------------------
+struct QueryArgs {
+    const int4 *nodes;
+    const float4 *leaves;
+    const uint2 *leaf_q;   // quantized leaf boxes (candidate mode)
+    const void *keys_sorted;
+    bool wide_keys;
+    const SegInfo *seg;
+    const SysInfo *sys;
+    int n;
+    int n_types;
+    int cap;
+    int *rows;
+    int *counts;
+    DevStatus *status;
+    int candidates;        // 1: Alg. 1 candidates, no exact leaf test
+    int block;
+    float r_list[64];      // [a][b] list radius
+    float rl2[64];         // fl(r * r)
+    float rs[64];          // padded search radius (rounded up)
+    float rs2[64];         // rs^2 rounded up
+};
+
+void launch_query(const QueryArgs &a, cudaStream_t s);
+
+// ---- Lennard-Jones (lj.cu) -----------------------------------------------
+struct LJArgs {
+    const float4 *pos;
+    const int *rows;
+    const int *counts;
+    int cap;
+    int n;
+    int n_types;
+    int n_sys;
+    const SysInfo *sys;
+    const int *blk_sys;    // [n_blocks] system of each block
+    const int *blk_first;  // [n_blocks] first particle of each block
+    int n_blocks;
+    const float *eps;
+    const float *sig;
+    float rc2[64];         // fl(r_cut * r_cut)
+    float *e;
+    float *F;
+    double *partials;      // [n_blocks][1 + 2 T^2]
+    double *U;
+    double *dE;
+    double *dS;
+    const int *sys_blk_start; // [n_sys + 1]
+};
+
+void launch_lj_forward(const LJArgs &a, cudaStream_t s);
+
+void launch_lj_backward(const double *g, const float *F, const double *dE, const double *dS,
+                        float *gpos, float *geps, float *gsig, int n, int n_sys, int n_types,
+                        const SysInfo *sys, const int *sys_off, cudaStream_t s);
+
+void launch_pack(const float *xyz, const int *types, int n, float4 *out, cudaStream_t s);
+
+}  // namespace qbvh
