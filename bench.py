@@ -117,11 +117,25 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    s = workloads.workload(WORKLOAD, seed=rank)
+    if args.n:
+        # smaller case of the same fluid (density, jitter, radius) for profiling only
+        s = workloads.jittered_lattice(args.n, 0.8, 0.25, seed=rank, r_cut=3.0, skin=0.3)
+    else:
+        s = workloads.workload(WORKLOAD, seed=rank)
     n = s.n
     pos4_host = torch.from_numpy(workloads.pack_float4(s.pos, s.types)).pin_memory()
     pos4 = pos4_host.cuda()
     nl = NeighborList(local)
+    if args.bundle:
+        nl.set_option(_lib.QBVH_OPT_BUNDLE, args.bundle)
+    if args.block:
+        nl.set_option(_lib.QBVH_OPT_QUERY_BLOCK, args.block)
+    if args.traversal >= 0:
+        nl.set_option(_lib.QBVH_OPT_TRAVERSAL, args.traversal)
+    if args.node_format >= 0:
+        nl.set_option(_lib.QBVH_OPT_NODE_FORMAT, args.node_format)
+    if args.lj_lanes:
+        nl.set_option(_lib.QBVH_OPT_LJ_LANES, args.lj_lanes)
     eps = torch.ones((1, 1), dtype=torch.float32, device="cuda")
     sig = torch.ones((1, 1), dtype=torch.float32, device="cuda")
     U = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -231,6 +245,10 @@ def run_ours(args):
                 "parallelism": f"replicas x{world}",
                 "bundle_k": nl.get_option(_lib.QBVH_OPT_BUNDLE),
                 "query_block": nl.get_option(_lib.QBVH_OPT_QUERY_BLOCK),
+                "traversal": ["thread_per_particle", "warp_per_32_particles"][
+                    nl.get_option(_lib.QBVH_OPT_TRAVERSAL)],
+                "node_format": ["quantized_10bit_16B", "fp32_32B"][nl.get_option(_lib.QBVH_OPT_NODE_FORMAT)],
+                "lj_lanes_per_particle": nl.get_option(_lib.QBVH_OPT_LJ_LANES),
             },
             "breakdown_ms": {"build": float(t_build.mean()), "query": float(t_query.mean()),
                              "lj": float(t_lj.mean())},
@@ -248,6 +266,8 @@ def run_ours(args):
             "clocks": clocks,
             "wall_s_timed": wall,
         }
+        if args.n:
+            out["config"]["workload"] = f"profiling case: LJ fluid N={n} rho=0.8 (not a bench result)"
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(s, samples=1)
         elif world == 1:
@@ -315,6 +335,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=0,
+                    help="profiling aid: run the same fluid with N particles instead of 2,097,152 "
+                         "(the line it prints is not a bench result)")
+    ap.add_argument("--bundle", type=int, default=0, help="subtree-collapse size K (0: library default)")
+    ap.add_argument("--block", type=int, default=0, help="traversal threads per block (0: library default)")
+    ap.add_argument("--lj-lanes", type=int, default=0, help="lanes per particle in the LJ pass (0: default)")
+    ap.add_argument("--node-format", type=int, default=-1,
+                    help="0: 10-bit quantized nodes, 1: FP32 nodes (-1: library default)")
+    ap.add_argument("--traversal", type=int, default=-1,
+                    help="0: one thread per particle, 1: one warp per 32 particles (-1: library default)")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)

@@ -81,8 +81,8 @@ int qbvh_destroy(qbvh_handle h);
 /* ---- tuning options (qbvh_set_option) ---------------------------------- */
 /* Subtree collapse (Sec. 2.3, final paragraph): internal nodes with at most K
  * leaves are traversed by testing their leaves directly.  K = 1 keeps the
- * paper's one-particle leaves.  Values 1..32, default 4.  Takes effect at the
- * next build. */
+ * paper's one-particle leaves.  Values 1..32, default 16.  Takes effect at
+ * the next build. */
 #define QBVH_OPT_BUNDLE 1
 /* Threads per block of the traversal kernel: 32..1024, multiple of 32,
  * default 128.  Takes effect at the next query. */
@@ -91,6 +91,18 @@ int qbvh_destroy(qbvh_handle h);
  * sphere overlaps, as Alg. 1 does (candidates, false positives included).
  * 0 (default) = exact list. */
 #define QBVH_OPT_CANDIDATES 3
+/* Traversal mapping: 0 = one thread per particle (Alg. 1 as written);
+ * 1 (default) = one warp per 32 consecutive Z-order particles walking the
+ * tree together (same rope walk, warp-uniform control flow, each lane testing
+ * its own sphere).  Both give the same list.  Takes effect at the next query. */
+#define QBVH_OPT_TRAVERSAL 4
+/* Node storage: 0 (default) = 16-byte nodes with 10-bit quantized bounds
+ * (Fig. 3b); 1 = 32-byte nodes with exact FP32 bounds (Fig. 3a).  Both give
+ * the same list.  Takes effect at the next build. */
+#define QBVH_OPT_NODE_FORMAT 5
+/* Lanes that share one particle's row in qbvh_lj_forward: 1, 2, 4, 8, 16 or
+ * 32 (default 8).  More lanes read a row in longer contiguous chunks. */
+#define QBVH_OPT_LJ_LANES 6
 
 int qbvh_set_option(qbvh_handle h, int option, int value);
 int qbvh_get_option(qbvh_handle h, int option, int *value);
@@ -136,8 +148,10 @@ int qbvh_build_batched(qbvh_handle h, const void *pos_dev, int n_total, int n_sy
  * exact FP32 distance test at the leaves, and compaction into rows.
  *
  * r_list_host : [n_types][n_types] list radii (r_cut + skin), symmetric,
- *               each 0 <= r < L/2 of every system (0 = type pair never listed).
- * cap         : initial row capacity, >= 1.
+ *               each 0 <= r < (L/2)(1 - 2^-20) for every system's L
+ *               (0 = type pair never listed).
+ * cap         : initial row capacity, >= 1; rounded up to a multiple of 4
+ *               (nlist_get reports the capacity in use).
  * max_retries : when some row has more than cap neighbors the capacity is
  *               raised to the largest count rounded up to 32 and the traversal
  *               rerun (tree reused), at most max_retries times.

@@ -28,6 +28,9 @@ QBVH_ERR_INTERNAL = 10
 QBVH_OPT_BUNDLE = 1
 QBVH_OPT_QUERY_BLOCK = 2
 QBVH_OPT_CANDIDATES = 3
+QBVH_OPT_TRAVERSAL = 4
+QBVH_OPT_NODE_FORMAT = 5
+QBVH_OPT_LJ_LANES = 6
 
 _lock = threading.Lock()
 _lib = None

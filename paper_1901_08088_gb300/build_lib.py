@@ -57,8 +57,17 @@ def _compile(src: str, force: bool, verbose: bool, extra: list[str]) -> str:
 
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+    """Build libqbvh.so.  Extra nvcc flags (tuning macros such as
+    -DQBVH_LEAF_BATCH=8) come from `extra` or the QBVH_NVCC_FLAGS variable;
+    changing them forces a rebuild."""
     os.makedirs(BUILD, exist_ok=True)
-    extra = list(extra or [])
+    extra = list(extra or []) + os.environ.get("QBVH_NVCC_FLAGS", "").split()
+    stamp = os.path.join(BUILD, "flags.txt")
+    flags_now = " ".join(extra)
+    if not os.path.exists(stamp) or open(stamp).read() != flags_now:
+        force = True
+        with open(stamp, "w") as fh:
+            fh.write(flags_now)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, force, verbose, extra), SOURCES))
     if force or _stale(LIB, objs):

@@ -45,9 +45,13 @@ struct qbvh_ctx {
     int device = 0;
     int fault = FAULT_NONE;
     // options
-    int bundle_k = 4;
+    int bundle_k = 16;
     int query_block = 128;
     int candidates = 0;
+    int traversal = 1;
+    int node_fmt = 0;      // 0: 10-bit quantized nodes (Fig. 3b), 1: FP32 nodes (Fig. 3a)
+    int lj_tpp = 8;        // lanes per particle in the LJ pass
+    int built_fmt = 0;     // node format of the last build
     // last build
     bool built = false;
     int n = 0, n_sys = 0, n_types = 0, n_seg = 0;
@@ -63,11 +67,12 @@ struct qbvh_ctx {
     int max_count = 0;
     float r_list[64];
     // device buffers
-    DevBuf keys[2], vals[2], sort_scratch, nodes, leaves, leaf_q, range, child, par_int, par_leaf, visit;
+    DevBuf keys[2], vals[2], sort_scratch, nodes, nodes32, leaves, leaf_q, range, child, par_int, par_leaf, visit;
     DevBuf seg, acc, seg_start, frames, sys, sys_off, status;
     DevBuf rows, counts;
     DevBuf lj_partials, lj_blk_sys, lj_blk_first, lj_sys_blk;
     std::vector<int> lj_layout_off;   // offsets the LJ block tables were built for
+    int lj_layout_tpp = 0;
     int lj_n_blocks = 0;
     // uploads cached by content
     std::vector<SysInfo> up_sys;
@@ -208,6 +213,7 @@ int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *of
     rc = rc ? rc : ensure(h, h->vals[1], nn * 4);
     rc = rc ? rc : ensure(h, h->sort_scratch, sort_scratch_bytes(n, passes));
     rc = rc ? rc : ensure(h, h->nodes, nn * sizeof(int4));
+    if (h->node_fmt == 1) rc = rc ? rc : ensure(h, h->nodes32, nn * 2 * sizeof(float4));
     rc = rc ? rc : ensure(h, h->leaves, nn * sizeof(float4));
     rc = rc ? rc : ensure(h, h->leaf_q, nn * sizeof(uint2));
     rc = rc ? rc : ensure(h, h->range, nn * sizeof(int2));
@@ -257,8 +263,10 @@ int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *of
     a.visit = reinterpret_cast<int *>(h->visit.p);
     a.leaf_q = reinterpret_cast<uint2 *>(h->leaf_q.p);
     a.nodes = reinterpret_cast<int4 *>(h->nodes.p);
+    a.nodes32 = h->node_fmt == 1 ? reinterpret_cast<float4 *>(h->nodes32.p) : nullptr;
     a.leaves = reinterpret_cast<float4 *>(h->leaves.p);
     a.status = reinterpret_cast<DevStatus *>(h->status.p);
+    h->built_fmt = h->node_fmt;
 
     launch_build_prepare(a, s);
     launch_morton(a, s);
@@ -280,7 +288,8 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
 {
     if (!h) return QBVH_ERR_INVALID_ARG;
     if (!h->built) return QBVH_ERR_NOT_BUILT;
-    if (!r_list_host || cap < 1) return QBVH_ERR_INVALID_ARG;
+    if (!r_list_host || cap < 1 || cap > (1 << 28)) return QBVH_ERR_INVALID_ARG;
+    cap = (cap + 3) & ~3;   // rows are written in 16-byte groups
     const int T = h->n_types;
     if ((long long)h->n * cap >= (1LL << 40)) return QBVH_ERR_INVALID_ARG;
     QueryArgs q;
@@ -289,7 +298,10 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
         for (int b = 0; b < T; ++b) {
             const float r = r_list_host[a * T + b];
             if (!(r >= 0.f) || !isfinite(r) || r != r_list_host[b * T + a]) return QBVH_ERR_INVALID_ARG;
-            if (h->n > 0 && r > 0.f && !(r < 0.5f * h->L_min)) return QBVH_ERR_CUTOFF_TOO_LARGE;
+            // below half the box by a relative 2^-20: then a pair is found under
+            // exactly one periodic image, the one the exact test selects
+            if (h->n > 0 && r > 0.f && !((double)r < 0.5 * (double)h->L_min * (1.0 - ldexp(1.0, -20))))
+                return QBVH_ERR_CUTOFF_TOO_LARGE;
             q.r_list[a * T + b] = r;
             q.rl2[a * T + b] = r * r;
             // padded search radius: covers FP32 rounding of the image position
@@ -305,6 +317,8 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
     DevStatus *st = reinterpret_cast<DevStatus *>(h->status.p);
     if (cudaMemsetAsync(&st->max_count, 0, sizeof(int), s) != cudaSuccess) return QBVH_ERR_CUDA;
     q.nodes = reinterpret_cast<const int4 *>(h->nodes.p);
+    q.nodes32 = reinterpret_cast<const float4 *>(h->nodes32.p);
+    q.node_fmt = h->built_fmt;
     q.leaves = reinterpret_cast<const float4 *>(h->leaves.p);
     q.leaf_q = reinterpret_cast<const uint2 *>(h->leaf_q.p);
     q.keys_sorted = h->keys[h->sorted].p;
@@ -318,6 +332,7 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
     q.counts = reinterpret_cast<int *>(h->counts.p);
     q.status = st;
     q.candidates = h->candidates;
+    q.traversal = h->traversal;
     q.block = h->query_block;
     launch_query(q, s);
     if (cudaMemcpyAsync(h->h_status, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -392,7 +407,7 @@ int qbvh_destroy(qbvh_handle h)
     {
         DeviceGuard g(h->device);
         cudaDeviceSynchronize();
-        DevBuf *all[] = {&h->keys[0], &h->keys[1], &h->vals[0], &h->vals[1], &h->sort_scratch, &h->nodes,
+        DevBuf *all[] = {&h->keys[0], &h->keys[1], &h->vals[0], &h->vals[1], &h->sort_scratch, &h->nodes, &h->nodes32,
                          &h->leaves, &h->leaf_q, &h->range, &h->child, &h->par_int, &h->par_leaf, &h->visit,
                          &h->seg, &h->acc, &h->seg_start, &h->frames, &h->sys, &h->sys_off, &h->status,
                          &h->rows, &h->counts, &h->lj_partials, &h->lj_blk_sys, &h->lj_blk_first,
@@ -420,6 +435,18 @@ int qbvh_set_option(qbvh_handle h, int option, int value)
         if (value != 0 && value != 1) return QBVH_ERR_INVALID_ARG;
         h->candidates = value;
         return QBVH_OK;
+    case QBVH_OPT_TRAVERSAL:
+        if (value != 0 && value != 1) return QBVH_ERR_INVALID_ARG;
+        h->traversal = value;
+        return QBVH_OK;
+    case QBVH_OPT_NODE_FORMAT:
+        if (value != 0 && value != 1) return QBVH_ERR_INVALID_ARG;
+        h->node_fmt = value;
+        return QBVH_OK;
+    case QBVH_OPT_LJ_LANES:
+        if (value < 1 || value > 32 || (value & (value - 1))) return QBVH_ERR_INVALID_ARG;
+        h->lj_tpp = value;
+        return QBVH_OK;
     default: return QBVH_ERR_INVALID_ARG;
     }
 }
@@ -431,6 +458,9 @@ int qbvh_get_option(qbvh_handle h, int option, int *value)
     case QBVH_OPT_BUNDLE: *value = h->bundle_k; return QBVH_OK;
     case QBVH_OPT_QUERY_BLOCK: *value = h->query_block; return QBVH_OK;
     case QBVH_OPT_CANDIDATES: *value = h->candidates; return QBVH_OK;
+    case QBVH_OPT_TRAVERSAL: *value = h->traversal; return QBVH_OK;
+    case QBVH_OPT_NODE_FORMAT: *value = h->node_fmt; return QBVH_OK;
+    case QBVH_OPT_LJ_LANES: *value = h->lj_tpp; return QBVH_OK;
     default: return QBVH_ERR_INVALID_ARG;
     }
 }
@@ -525,9 +555,9 @@ int qbvh_lj_forward(qbvh_handle h, const void *pos_dev, const float *eps_dev, co
     }
     DeviceGuard g(h->device);
     // block tables: every block covers particles of one system
-    const int B = lj_block_size();
+    const int B = lj_block_size() / h->lj_tpp;   // particles per block
     int rc = QBVH_OK;
-    if (h->lj_layout_off != h->off || h->lj_blk_sys.p == nullptr) {
+    if (h->lj_layout_off != h->off || h->lj_layout_tpp != h->lj_tpp || h->lj_blk_sys.p == nullptr) {
         std::vector<int> blk_sys, blk_first, sys_blk(h->n_sys + 1, 0);
         for (int k = 0; k < h->n_sys; ++k) {
             sys_blk[k] = (int)blk_sys.size();
@@ -552,6 +582,7 @@ int qbvh_lj_forward(qbvh_handle h, const void *pos_dev, const float *eps_dev, co
             cudaMemcpyAsync(h->lj_sys_blk.p, sys_blk.data(), sys_blk.size() * 4, cudaMemcpyHostToDevice, stream))
             return QBVH_ERR_CUDA;
         h->lj_layout_off = h->off;
+        h->lj_layout_tpp = h->lj_tpp;
     }
     const int np = 1 + 2 * T * T;
     rc = ensure(h, h->lj_partials, (size_t)(h->lj_n_blocks > 0 ? h->lj_n_blocks : 1) * np * 8);
@@ -567,6 +598,7 @@ int qbvh_lj_forward(qbvh_handle h, const void *pos_dev, const float *eps_dev, co
     a.blk_sys = reinterpret_cast<const int *>(h->lj_blk_sys.p);
     a.blk_first = reinterpret_cast<const int *>(h->lj_blk_first.p);
     a.n_blocks = h->lj_n_blocks;
+    a.tpp = h->lj_tpp;
     a.eps = eps_dev;
     a.sig = sig_dev;
     a.e = e_dev;

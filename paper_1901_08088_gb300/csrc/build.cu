@@ -347,7 +347,9 @@ __device__ __forceinline__ int rope_after(const int2 *range, int last, int hi)
     return ~k;
 }
 
-template <bool WIDE>
+__device__ __forceinline__ float clear_sign(float x) { return __int_as_float(__float_as_int(x) & 0x7FFFFFFF); }
+
+template <bool WIDE, bool F32>
 __global__ void __launch_bounds__(kBlock) fit_kernel(const BuildArgs a)
 {
     const int k = blockIdx.x * kBlock + threadIdx.x;
@@ -411,6 +413,31 @@ __global__ void __launch_bounds__(kBlock) fit_kernel(const BuildArgs a)
         w.z = bundle ? r.x : c.x;
         w.w = rope_after(a.range, r.y, hi);
         __stcg(a.nodes + node, w);
+        if (F32) {
+            // exact FP32 AABB: min / max of the children's boxes (Fig. 3a layout)
+            float4 lo_a, hi_a, lo_b, hi_b;
+            if (c.x >= 0) {
+                lo_a = __ldcg(a.nodes32 + 2 * (size_t)c.x);
+                hi_a = __ldcg(a.nodes32 + 2 * (size_t)c.x + 1);
+                lo_a.x = clear_sign(lo_a.x);
+            } else {
+                lo_a = hi_a = __ldcg(a.leaves + ~c.x);
+            }
+            if (c.y >= 0) {
+                lo_b = __ldcg(a.nodes32 + 2 * (size_t)c.y);
+                hi_b = __ldcg(a.nodes32 + 2 * (size_t)c.y + 1);
+                lo_b.x = clear_sign(lo_b.x);
+            } else {
+                lo_b = hi_b = __ldcg(a.leaves + ~c.y);
+            }
+            float lx = fminf(lo_a.x, lo_b.x);
+            if (bundle) lx = __int_as_float(__float_as_int(lx) | 0x80000000);
+            __stcg(a.nodes32 + 2 * (size_t)node,
+                   make_float4(lx, fminf(lo_a.y, lo_b.y), fminf(lo_a.z, lo_b.z), __int_as_float(w.z)));
+            __stcg(a.nodes32 + 2 * (size_t)node + 1,
+                   make_float4(fmaxf(hi_a.x, hi_b.x), fmaxf(hi_a.y, hi_b.y), fmaxf(hi_a.z, hi_b.z),
+                               __int_as_float(w.w)));
+        }
         node = a.par_int[node];
     }
 }
@@ -451,10 +478,14 @@ void launch_karras(const BuildArgs &a, cudaStream_t s)
 void launch_fit(const BuildArgs &a, cudaStream_t s)
 {
     if (a.n == 0) return;
-    if (a.wide_keys)
-        fit_kernel<true><<<blocks_for(a.n, kBlock), kBlock, 0, s>>>(a);
-    else
-        fit_kernel<false><<<blocks_for(a.n, kBlock), kBlock, 0, s>>>(a);
+    const int g = blocks_for(a.n, kBlock);
+    if (a.wide_keys) {
+        if (a.nodes32) fit_kernel<true, true><<<g, kBlock, 0, s>>>(a);
+        else fit_kernel<true, false><<<g, kBlock, 0, s>>>(a);
+    } else {
+        if (a.nodes32) fit_kernel<false, true><<<g, kBlock, 0, s>>>(a);
+        else fit_kernel<false, false><<<g, kBlock, 0, s>>>(a);
+    }
 }
 
 }  // namespace qbvh

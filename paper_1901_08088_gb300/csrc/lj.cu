@@ -27,7 +27,9 @@ __device__ __forceinline__ float mi_component(float d, float L, float Linv)
     return __fsub_rn(d, __fmul_rn(L, rintf(__fmul_rn(d, Linv))));
 }
 
-template <int T>
+// TPP lanes share one particle: lane r of the group takes row entries
+// r, r + TPP, ..., so that a group reads its row in contiguous chunks.
+template <int T, int TPP>
 __global__ void __launch_bounds__(kLJBlock) lj_forward_kernel(const __grid_constant__ LJArgs a)
 {
     constexpr int NP = 1 + 2 * T * T;
@@ -48,7 +50,8 @@ __global__ void __launch_bounds__(kLJBlock) lj_forward_kernel(const __grid_const
     __syncthreads();
     const int sys = a.blk_sys[blockIdx.x];
     const SysInfo sy = a.sys[sys];
-    const int i = a.blk_first[blockIdx.x] + tid;
+    const int sub = tid % TPP;
+    const int i = a.blk_first[blockIdx.x] + tid / TPP;
     const bool active = i < sy.offset + sy.count;
     float e = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
     float gE[T], gS[T];
@@ -61,7 +64,7 @@ __global__ void __launch_bounds__(kLJBlock) lj_forward_kernel(const __grid_const
         ta = ta < 0 ? 0 : (ta >= T ? T - 1 : ta);
         const int c = min(__ldg(a.counts + i), a.cap);
         const int *row = a.rows + (size_t)i * a.cap;
-        for (int k = 0; k < c; ++k) {
+        for (int k = sub; k < c; k += TPP) {
             const int j = __ldg(row + k);
             if ((unsigned)j >= (unsigned)a.n) continue;   // never for a list from the traversal
             const float4 pj = __ldg(a.pos + j);
@@ -73,11 +76,12 @@ __global__ void __launch_bounds__(kLJBlock) lj_forward_kernel(const __grid_const
             const float dz = mi_component(__fsub_rn(pj.z, pi.z), sy.L, sy.Linv);
             const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
             if (!(r2 < s_rc2[p])) continue;
-            const float s2 = s_sig2[p] / r2;
+            const float inv_r2 = __frcp_rn(r2);
+            const float s2 = s_sig2[p] * inv_r2;
             const float s6 = s2 * s2 * s2;
             const float uE = 4.f * (s6 * s6 - s6) - s_phic[p];   // u / eps
             const float q = 2.f * s6 * s6 - s6;
-            const float w = 24.f * s_eps[p] * q / r2;
+            const float w = 24.f * s_eps[p] * q * inv_r2;
             e += s_eps[p] * uE;
             fx -= w * dx;
             fy -= w * dy;
@@ -90,24 +94,39 @@ __global__ void __launch_bounds__(kLJBlock) lj_forward_kernel(const __grid_const
                 }
             }
         }
-        e *= 0.5f;
-        if (a.e) a.e[i] = e;
+    }
+    // per-particle results: FP32 sums over the group's lanes
+    float ei = e, fxi = fx, fyi = fy, fzi = fz;
+#pragma unroll
+    for (int o = TPP / 2; o > 0; o >>= 1) {
+        ei += __shfl_xor_sync(0xFFFFFFFFu, ei, o);
+        fxi += __shfl_xor_sync(0xFFFFFFFFu, fxi, o);
+        fyi += __shfl_xor_sync(0xFFFFFFFFu, fyi, o);
+        fzi += __shfl_xor_sync(0xFFFFFFFFu, fzi, o);
+    }
+    if (active && sub == 0) {
+        if (a.e) a.e[i] = 0.5f * ei;
         if (a.F) {
-            a.F[3 * (size_t)i] = fx;
-            a.F[3 * (size_t)i + 1] = fy;
-            a.F[3 * (size_t)i + 2] = fz;
+            a.F[3 * (size_t)i] = fxi;
+            a.F[3 * (size_t)i + 1] = fyi;
+            a.F[3 * (size_t)i + 2] = fzi;
         }
     }
-    // FP64 block reduction of energy and the parameter-gradient contributions
+    // FP64 block reduction of the energy and the parameter-gradient terms
     double v[NP];
-    v[0] = (double)e;
+    v[0] = 0.5 * (double)e;
 #pragma unroll
     for (int q = 1; q < NP; ++q) v[q] = 0.0;
     if (active) {
 #pragma unroll
         for (int b = 0; b < T; ++b) {
-            v[1 + ta * T + b] = 0.5 * (double)gE[b];
-            v[1 + T * T + ta * T + b] = 0.5 * (double)gS[b];
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                if (t == ta) {
+                    v[1 + t * T + b] = 0.5 * (double)gE[b];
+                    v[1 + T * T + t * T + b] = 0.5 * (double)gS[b];
+                }
+            }
         }
     }
     const int lane = tid & 31, warp = tid >> 5;
@@ -191,18 +210,31 @@ __global__ void pack_kernel(const float *xyz, const int *types, int n, float4 *o
 
 int lj_block_size() { return kLJBlock; }
 
+template <int T>
+static void launch_lj_t(const LJArgs &a, cudaStream_t s)
+{
+    switch (a.tpp) {
+    case 1: lj_forward_kernel<T, 1><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
+    case 2: lj_forward_kernel<T, 2><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
+    case 4: lj_forward_kernel<T, 4><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
+    case 8: lj_forward_kernel<T, 8><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
+    case 16: lj_forward_kernel<T, 16><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
+    default: lj_forward_kernel<T, 32><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
+    }
+}
+
 void launch_lj_forward(const LJArgs &a, cudaStream_t s)
 {
     if (a.n_blocks > 0) {
         switch (a.n_types) {
-        case 1: lj_forward_kernel<1><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
-        case 2: lj_forward_kernel<2><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
-        case 3: lj_forward_kernel<3><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
-        case 4: lj_forward_kernel<4><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
-        case 5: lj_forward_kernel<5><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
-        case 6: lj_forward_kernel<6><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
-        case 7: lj_forward_kernel<7><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
-        default: lj_forward_kernel<8><<<a.n_blocks, kLJBlock, 0, s>>>(a); break;
+        case 1: launch_lj_t<1>(a, s); break;
+        case 2: launch_lj_t<2>(a, s); break;
+        case 3: launch_lj_t<3>(a, s); break;
+        case 4: launch_lj_t<4>(a, s); break;
+        case 5: launch_lj_t<5>(a, s); break;
+        case 6: launch_lj_t<6>(a, s); break;
+        case 7: launch_lj_t<7>(a, s); break;
+        default: launch_lj_t<8>(a, s); break;
         }
     }
     const int T = a.n_types;

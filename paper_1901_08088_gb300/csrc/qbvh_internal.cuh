@@ -12,6 +12,9 @@
 //   visit    int32 arrival counter of internal node k (bottom-up fit)
 //   leaf_q   uint2 quantized AABB {lo, hi} of leaf k
 //   nodes    int4  {lo | bundle<<31, hi, left or first leaf, rope}   (Fig. 3b)
+//   nodes32  2 x float4 per internal node, the uncompressed layout of Fig. 3a:
+//            {lo.x (sign bit = bundle), lo.y, lo.z, left or first leaf},
+//            {hi.x, hi.y, hi.z, rope}; written only when that format is chosen
 //   leaves   float4 {x, y, z, original index | rope-is-internal<<31}
 // Node ids: k >= 0 internal node k, ~k (negative) leaf k, QBVH_END = INT32_MIN.
 #pragma once
@@ -85,6 +88,7 @@ struct BuildArgs {
     int *visit;
     uint2 *leaf_q;
     int4 *nodes;
+    float4 *nodes32;     // [2n] FP32 nodes or nullptr
     float4 *leaves;
     DevStatus *status;
 };
@@ -114,6 +118,8 @@ int radix_sort_pairs(bool wide, void *keys_a, void *keys_b, int *vals_a, int *va
 // ---- traversal (query.cu) ------------------------------------------------
 struct QueryArgs {
     const int4 *nodes;
+    const float4 *nodes32;  // FP32 node format (node_fmt == 1)
+    int node_fmt;
     const float4 *leaves;
     const uint2 *leaf_q;   // quantized leaf boxes (candidate mode)
     const void *keys_sorted;
@@ -127,6 +133,7 @@ struct QueryArgs {
     int *counts;
     DevStatus *status;
     int candidates;        // 1: Alg. 1 candidates, no exact leaf test
+    int traversal;         // 0: one thread per particle, 1: one warp per 32 particles
     int block;
     float r_list[64];      // [a][b] list radius
     float rl2[64];         // fl(r * r)
@@ -149,6 +156,7 @@ struct LJArgs {
     const int *blk_sys;    // [n_blocks] system of each block
     const int *blk_first;  // [n_blocks] first particle of each block
     int n_blocks;
+    int tpp;               // lanes per particle (1, 2, 4, 8, 16, 32)
     const float *eps;
     const float *sig;
     float rc2[64];         // fl(r_cut * r_cut)

@@ -1,125 +1,285 @@
 // Neighbor-list traversal (Alg. 1 of the paper).
 //
-// One thread per particle, particles taken in Z-order so that the threads of a
-// warp walk nearby parts of the tree (Sec. 3).  For every tree the particle
-// interacts with (one tree per type, per-type-pair radius):
-//   1. test the 27 periodic images of the search sphere against the root
-//      AABB and keep the overlapping ones in a bitset (Sec. 2.3; Alg. 1 image
-//      loop);
+// Particles are taken in Z-order so that neighbouring threads walk nearby
+// parts of the tree (Sec. 3).  For every tree the particle interacts with (one
+// tree per type, per-type-pair radius):
+//   1. test the 27 periodic images of the search sphere against the root AABB
+//      and keep the overlapping ones in a bitset (Sec. 2.3; Alg. 1 image loop);
 //   2. for each image: stackless traversal from the root -- on overlap descend
 //      to the left child, otherwise follow the rope, stop at the end marker
 //      (Sec. 2.1; Alg. 1 inner loop);
-//   3. node test: decompress the 10-bit bounds outward (lower bound rounded
-//      down, upper up, Sec. 2.3 and Sec. 3) and test the sphere against the
-//      box through the nearest point y = min(max(x, a), b) (Eq. 2), with every
-//      rounding in the direction that can only enlarge the overlap;
-//   4. leaf: the paper lists the particle as soon as the sphere overlaps the
-//      leaf (Sec. 2.3), accepting false positives it allows to be filtered
-//      later; here the exact FP32 minimum-image test is that filter, so the
-//      list is exact.  Internal nodes with at most K leaves ("bundles", the
-//      subtree collapse suggested at the end of Sec. 2.3) are tested leaf by
-//      leaf without descending.
+//   3. node test: the sphere against the node's box through the nearest point
+//      y = min(max(x, a), b) (Eq. 2).  Quantized bounds are decompressed
+//      outward first (lower bound rounded down, upper up; Sec. 2.3, Sec. 3);
+//      the squared distance is rounded down, so a true overlap is never
+//      rejected;
+//   4. leaf: the paper lists the particle when the sphere overlaps the leaf
+//      (Sec. 2.3) and allows the false positives to be filtered later; here
+//      the exact FP32 distance test is that filter, so the list is exact.
+//      Internal nodes with at most K leaves ("bundles", the subtree collapse
+//      suggested at the end of Sec. 2.3) are not descended: their leaves,
+//      contiguous in Z-order, are tested directly.
 //
-// Conservativeness.  The sphere radius is padded on the host:
-//   r_search = r_list (1 + 2^-20) + 2^-19 L, rounded up, r_search^2 rounded up.
-// If the exact test accepts j for image n (d2 < fl(r_list^2)), rounding in
-// that expression and in the image position fl(x_i + n L) moves the real
-// distance |x_i + nL - x_j| by at most r_list * 4.1 u + 5.2 u L (u = 2^-24),
-// below the padding, and x_j lies in every decoded ancestor box, so every
-// ancestor passes the round-down sphere test: no pair is lost.
+// Two mappings of particles to threads:
+//   query_thread_kernel: one thread per particle, Alg. 1 as written;
+//   query_warp_kernel:   one warp per 32 consecutive Z-order particles.  The
+//     warp takes the same rope walk together: at every node each lane tests
+//     its own sphere and the warp descends when any lane overlaps; at a leaf
+//     or bundle every lane runs the exact test on the same (broadcast) leaf.
+//     Control flow is warp-uniform.
 //
-// Duplicates.  A leaf may overlap the padded sphere of two images; it is
-// accepted only under the image n = rint(fl((x_j - x_i) / L)) that the exact
-// expression itself selects, so each j appears at most once per row.
+// Conservativeness.  The search radius is padded on the host:
+//   r_search = r_list (1 + 2^-20) + 2^-19 L, rounded up; r_search^2 rounded up.
+// If the exact test accepts j under image n, rounding in that test and in the
+// image centre fl(x_i + nL) moves the real distance |x_i + nL - x_j| by at
+// most r_list * 4.1 u + 5.2 u L (u = 2^-24), below the padding; x_j lies in
+// every decoded ancestor box, so every ancestor passes: no pair is lost.
+//
+// Exact test and image choice.  The list's decision expression is
+//   dx = fl(xj - xi); dx = fl(dx - fl(L rint(fl(dx Linv)))), same for y, z,
+//   d2 = fl(fl(fl(dx^2) + fl(dy^2)) + fl(dz^2)) < fl(r^2).
+// Under image n the kernel computes d2 from fl(fl(xj - xi) - nL) and accepts
+// when d2 < fl(r^2), without evaluating rint.  This is the same decision: the
+// host requires r < (L/2)(1 - 2^-20).  If the shifted d2 < fl(r^2) then every
+// shifted component satisfies |dx'| < r (1 + 2.1 u) < (L/2)(1 - 2^-21); for
+// n != 0, Sterbenz's lemma makes fl(dx - nL) exact, so dx = nL + dx' and
+// fl(dx * Linv) lies strictly inside (n - 1/2, n + 1/2): rint gives n, the
+// expression's own choice.  Hence a pair is accepted under exactly one image,
+// the one rint selects, with the same d2 -- and rows hold no duplicates.
 #include "qbvh_internal.cuh"
 
 namespace qbvh {
 
 namespace {
 
+constexpr unsigned FULL = 0xFFFFFFFFu;
 struct Frame {
     float rx, ry, rz;   // R_lo
     float hx, hy, hz;   // bin width
 };
 
-__device__ __forceinline__ float q_at(unsigned w, int shift) { return (float)((w >> shift) & 1023u); }
+// A node's bounds (decoded to FP32, outward) and links.
+struct Node {
+    float lx, ly, lz, hx, hy, hz;
+    int left;     // left child id, or first leaf index of a bundle
+    int rope;
+    bool bundle;
+};
 
-// Sphere (centre p, squared radius rs2) against the quantized box of a node.
-// Decoded bounds are rounded outward and the squared distance to the box is a
-// lower bound, so a true overlap is never rejected.
-__device__ __forceinline__ bool overlap_q(float px, float py, float pz, unsigned wlo, unsigned whi,
-                                          const Frame &f, float rs2)
+// 10-bit field -> float, exact: OR the value into the mantissa of 2^23, then
+// subtract 2^23.
+__device__ __forceinline__ float q_at(unsigned w, int shift)
 {
-    const float lox = __fmaf_rd(q_at(wlo, 20), f.hx, f.rx);
-    const float loy = __fmaf_rd(q_at(wlo, 10), f.hy, f.ry);
-    const float loz = __fmaf_rd(q_at(wlo, 0), f.hz, f.rz);
-    const float hix = __fmaf_ru(q_at(whi, 20), f.hx, f.rx);
-    const float hiy = __fmaf_ru(q_at(whi, 10), f.hy, f.ry);
-    const float hiz = __fmaf_ru(q_at(whi, 0), f.hz, f.rz);
-    const float gx = fmaxf(fmaxf(__fsub_rd(lox, px), __fsub_rd(px, hix)), 0.f);
-    const float gy = fmaxf(fmaxf(__fsub_rd(loy, py), __fsub_rd(py, hiy)), 0.f);
-    const float gz = fmaxf(fmaxf(__fsub_rd(loz, pz), __fsub_rd(pz, hiz)), 0.f);
+    return __uint_as_float(((w >> shift) & 1023u) | 0x4B000000u) - 8388608.f;
+}
+
+__device__ __forceinline__ Node decode_q(const int4 w, const Frame &f)
+{
+    Node n;
+    const unsigned lo = (unsigned)w.x, hi = (unsigned)w.y;
+    n.lx = __fmaf_rd(q_at(lo, 20), f.hx, f.rx);
+    n.ly = __fmaf_rd(q_at(lo, 10), f.hy, f.ry);
+    n.lz = __fmaf_rd(q_at(lo, 0), f.hz, f.rz);
+    n.hx = __fmaf_ru(q_at(hi, 20), f.hx, f.rx);
+    n.hy = __fmaf_ru(q_at(hi, 10), f.hy, f.ry);
+    n.hz = __fmaf_ru(q_at(hi, 0), f.hz, f.rz);
+    n.left = w.z;
+    n.rope = w.w;
+    n.bundle = w.x < 0;
+    return n;
+}
+
+__device__ __forceinline__ Node decode_f(const float4 a, const float4 b)
+{
+    Node n;
+    n.bundle = __float_as_int(a.x) < 0;
+    n.lx = __int_as_float(__float_as_int(a.x) & 0x7FFFFFFF);
+    n.ly = a.y;
+    n.lz = a.z;
+    n.hx = b.x;
+    n.hy = b.y;
+    n.hz = b.z;
+    n.left = __float_as_int(a.w);
+    n.rope = __float_as_int(b.w);
+    return n;
+}
+
+// Raw words of a node, loaded ahead of use.
+struct Raw {
+    int4 q;
+    float4 a, b;
+};
+
+template <int FMT>
+__device__ __forceinline__ Raw load_raw(const QueryArgs &A, int id)
+{
+    Raw r;
+    if (FMT == 0) {
+        r.q = __ldg(A.nodes + id);
+    } else {
+        r.a = __ldg(A.nodes32 + 2 * (size_t)id);
+        r.b = __ldg(A.nodes32 + 2 * (size_t)id + 1);
+    }
+    return r;
+}
+
+template <int FMT>
+__device__ __forceinline__ Node decode(const Raw &r, const Frame &f)
+{
+    if (FMT == 0) return decode_q(r.q, f);
+    return decode_f(r.a, r.b);
+}
+
+// Sphere (centre p, squared radius rs2) against a box: lower bound of the
+// squared distance from p to the box, compared with the rounded-up rs2.
+__device__ __forceinline__ bool overlap(float px, float py, float pz, const Node &n, float rs2)
+{
+    const float gx = fmaxf(fmaxf(__fsub_rd(n.lx, px), __fsub_rd(px, n.hx)), 0.f);
+    const float gy = fmaxf(fmaxf(__fsub_rd(n.ly, py), __fsub_rd(py, n.hy)), 0.f);
+    const float gz = fmaxf(fmaxf(__fsub_rd(n.lz, pz), __fsub_rd(pz, n.hz)), 0.f);
     const float d2 = __fmaf_rd(gx, gx, __fmaf_rd(gy, gy, __fmul_rd(gz, gz)));
     return d2 <= rs2;
 }
 
-// rint(t) == n for n in {-1, 0, 1} and |t| < 1.5 (always true for valid
-// positions), written as range tests; rint rounds half to even, so +-0.5 -> 0.
-__device__ __forceinline__ bool image_is(float t, int n)
+__device__ __forceinline__ bool overlap_q(float px, float py, float pz, uint2 q, const Frame &f, float rs2)
 {
-    return n == 0 ? (fabsf(t) <= 0.5f) : (n > 0 ? (t > 0.5f) : (t < -0.5f));
+    const Node n = decode_q(make_int4((int)q.x, (int)q.y, 0, 0), f);
+    return overlap(px, py, pz, n, rs2);
 }
 
-struct Ctx {
-    float xi, yi, zi;   // own position
-    int self;           // own sorted index
-    float L, Linv;
-    float rl2;
-    int nx, ny, nz;     // current image
-    float nLx, nLy, nLz;
+// Row writer.  Entries past cap are counted, not written.  (Gathering four
+// entries into one 16-byte store was measured slower: the extra selects and
+// registers cost more than the narrower stores.)
+struct Row {
     int *row;
     int cap;
     int count;
+
+    __device__ __forceinline__ void push(int j)
+    {
+        if (count < cap) row[count] = j;
+        ++count;
+    }
 };
 
-// The exact FP32 minimum-image test (pinned expression) for leaf j under the
-// current image; appends the original index on success.
-__device__ __forceinline__ void exact_leaf(Ctx &c, int j, const float4 q)
+struct Query {
+    float xi, yi, zi;     // own position
+    int self;             // own sorted index
+    float nLx, nLy, nLz;  // image shift n L
+    float px, py, pz;     // image centre fl(x_i + n L)
+    float rl2;
+};
+
+// The exact test of leaf j under the current image (see the header comment).
+__device__ __forceinline__ void exact_leaf(const Query &c, Row &out, int j, const float4 q)
 {
-    if (j == c.self) return;
-    float dx = __fsub_rn(q.x, c.xi);
-    float dy = __fsub_rn(q.y, c.yi);
-    float dz = __fsub_rn(q.z, c.zi);
-    if (!image_is(__fmul_rn(dx, c.Linv), c.nx) || !image_is(__fmul_rn(dy, c.Linv), c.ny) ||
-        !image_is(__fmul_rn(dz, c.Linv), c.nz))
-        return;
-    dx = __fsub_rn(dx, c.nLx);
-    dy = __fsub_rn(dy, c.nLy);
-    dz = __fsub_rn(dz, c.nLz);
+    const float dx = __fsub_rn(__fsub_rn(q.x, c.xi), c.nLx);
+    const float dy = __fsub_rn(__fsub_rn(q.y, c.yi), c.nLy);
+    const float dz = __fsub_rn(__fsub_rn(q.z, c.zi), c.nLz);
     const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-    if (d2 < c.rl2) {
-        if (c.count < c.cap) c.row[c.count] = __float_as_int(q.w) & 0x7FFFFFFF;
-        ++c.count;
-    }
+    if (d2 < c.rl2 && j != c.self) out.push(__float_as_int(q.w) & 0x7FFFFFFF);
 }
 
 // Alg. 1 without the exact filter: list j when the sphere overlaps its
 // quantized leaf box (false positives included).
-__device__ __forceinline__ void candidate_leaf(Ctx &c, int j, const float4 q, const uint2 lq, const Frame &f,
-                                               float px, float py, float pz, float rs2)
+__device__ __forceinline__ void candidate_leaf(const Query &c, Row &out, int j, const float4 q, const uint2 lq,
+                                               const Frame &f, float rs2)
 {
-    if (j == c.self) return;
-    if (overlap_q(px, py, pz, lq.x, lq.y, f, rs2)) {
-        if (c.count < c.cap) c.row[c.count] = __float_as_int(q.w) & 0x7FFFFFFF;
-        ++c.count;
-    }
+    if (j != c.self && overlap_q(c.px, c.py, c.pz, lq, f, rs2)) out.push(__float_as_int(q.w) & 0x7FFFFFFF);
 }
 
-template <bool WIDE, bool CAND>
-__global__ void query_kernel(const __grid_constant__ QueryArgs a)
+template <bool CAND>
+__device__ __forceinline__ void test_leaf(const QueryArgs &A, const Query &c, Row &out, int j, const float4 q,
+                                          const Frame &f, float rs2)
 {
-    const uint2 *__restrict__ leaf_q = a.leaf_q;
-    __shared__ int s_max[32];
+    if (CAND)
+        candidate_leaf(c, out, j, q, __ldg(A.leaf_q + j), f, rs2);
+    else
+        exact_leaf(c, out, j, q);
+}
+
+// 27-bit set of the periodic images whose padded search sphere overlaps the
+// root AABB of a tree (Sec. 2.3): bit 9 (nx+1) + 3 (ny+1) + (nz+1).
+__device__ __forceinline__ unsigned image_mask(float x, float y, float z, float L, const SegInfo &g, float rs2)
+{
+    float gap[3][3];
+    const float xs[3] = {x, y, z};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const float p = (m == 1) ? xs[d] : __fadd_rn(xs[d], (m == 0) ? -L : L);
+            gap[d][m] = fmaxf(fmaxf(__fsub_rd(g.rlo[d], p), __fsub_rd(p, g.rhi[d])), 0.f);
+        }
+    }
+    unsigned mask = 0u;
+#pragma unroll
+    for (int mx = 0; mx < 3; ++mx)
+#pragma unroll
+        for (int my = 0; my < 3; ++my)
+#pragma unroll
+            for (int mz = 0; mz < 3; ++mz) {
+                const float d2 = __fmaf_rd(gap[0][mx], gap[0][mx],
+                                           __fmaf_rd(gap[1][my], gap[1][my], __fmul_rd(gap[2][mz], gap[2][mz])));
+                if (d2 <= rs2) mask |= 1u << (mx * 9 + my * 3 + mz);
+            }
+    return mask;
+}
+
+__device__ __forceinline__ void set_image(Query &c, int img, float L)
+{
+    const int nx = img / 9 - 1, ny = (img / 3) % 3 - 1, nz = img % 3 - 1;
+    c.nLx = nx == 0 ? 0.f : (nx > 0 ? L : -L);
+    c.nLy = ny == 0 ? 0.f : (ny > 0 ? L : -L);
+    c.nLz = nz == 0 ? 0.f : (nz > 0 ? L : -L);
+    c.px = nx == 0 ? c.xi : __fadd_rn(c.xi, c.nLx);
+    c.py = ny == 0 ? c.yi : __fadd_rn(c.yi, c.nLy);
+    c.pz = nz == 0 ? c.zi : __fadd_rn(c.zi, c.nLz);
+}
+
+template <bool WIDE>
+__device__ __forceinline__ int seg_of_sorted(const QueryArgs &a, int s)
+{
+    if (WIDE) return (int)(__ldg(reinterpret_cast<const unsigned long long *>(a.keys_sorted) + s) >> 30);
+    if (a.n_types > 1) return (int)(__ldg(reinterpret_cast<const unsigned *>(a.keys_sorted) + s) >> 30);
+    return 0;
+}
+
+__device__ __forceinline__ Frame frame_of(const SegInfo &g)
+{
+    Frame f;
+    f.rx = g.rlo[0];
+    f.ry = g.rlo[1];
+    f.rz = g.rlo[2];
+    f.hx = g.h[0];
+    f.hy = g.h[1];
+    f.hz = g.h[2];
+    return f;
+}
+
+// node id outside the tree [start, last] -> broken structure
+__device__ __forceinline__ bool bad_node(int node, const SegInfo &g, int last)
+{
+    return node >= 0 ? (node < g.start || node > last) : (~node < g.start || ~node > last);
+}
+
+// Largest row count: one atomic per warp, skipped when it cannot raise the maximum.
+__device__ __forceinline__ void warp_max_count(int my_count, DevStatus *status)
+{
+    const int m = __reduce_max_sync(FULL, my_count);
+    if ((threadIdx.x & 31) == 0 && m > 0 && m > __ldcg(&status->max_count)) atomicMax(&status->max_count, m);
+}
+
+// Last leaf of a bundle: the leaf before the rope target, or the tree's last leaf.
+__device__ __forceinline__ int bundle_last(const Node &nd, int last)
+{
+    return (nd.rope == QBVH_END) ? last : ((nd.rope >= 0 ? nd.rope : ~nd.rope) - 1);
+}
+
+// ---- one thread per particle: Alg. 1 as written -------------------------
+template <bool WIDE, bool CAND, int FMT>
+__global__ void query_thread_kernel(const __grid_constant__ QueryArgs a)
+{
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     int my_count = 0;
     if (s < a.n) {
@@ -129,26 +289,21 @@ __global__ void query_kernel(const __grid_constant__ QueryArgs a)
             atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
             i_orig = s;
         }
-        int seg_i = 0;
-        if (WIDE)
-            seg_i = (int)(__ldg(reinterpret_cast<const unsigned long long *>(a.keys_sorted) + s) >> 30);
-        else if (a.n_types > 1)
-            seg_i = (int)(__ldg(reinterpret_cast<const unsigned *>(a.keys_sorted) + s) >> 30);
+        const int seg_i = seg_of_sorted<WIDE>(a, s);
         const int T = a.n_types;
         const int sys = seg_i / T;
         const int ta = seg_i - sys * T;
-        const SysInfo sy = a.sys[sys];
+        const float L = a.sys[sys].L;
 
-        Ctx c;
+        Query c;
         c.xi = me.x;
         c.yi = me.y;
         c.zi = me.z;
         c.self = s;
-        c.L = sy.L;
-        c.Linv = sy.Linv;
-        c.row = a.rows + (size_t)i_orig * a.cap;
-        c.cap = a.cap;
-        c.count = 0;
+        Row out;
+        out.row = a.rows + (size_t)i_orig * a.cap;
+        out.cap = a.cap;
+        out.count = 0;
 
         for (int tb = 0; tb < T; ++tb) {
             const float rl = a.r_list[ta * T + tb];
@@ -157,107 +312,149 @@ __global__ void query_kernel(const __grid_constant__ QueryArgs a)
             if (g.count == 0) continue;
             c.rl2 = a.rl2[ta * T + tb];
             const float rs2 = a.rs2[ta * T + tb];
-            Frame f;
-            f.rx = g.rlo[0];
-            f.ry = g.rlo[1];
-            f.rz = g.rlo[2];
-            f.hx = g.h[0];
-            f.hy = g.h[1];
-            f.hz = g.h[2];
-            // per-axis lower bounds of the gap between each image and the root
-            float gap[3][3];
-            const float xs[3] = {me.x, me.y, me.z};
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-#pragma unroll
-                for (int m = 0; m < 3; ++m) {
-                    const float p = (m == 1) ? xs[d] : __fadd_rn(xs[d], (m == 0) ? -c.L : c.L);
-                    gap[d][m] = fmaxf(fmaxf(__fsub_rd(g.rlo[d], p), __fsub_rd(p, g.rhi[d])), 0.f);
-                }
-            }
-            unsigned mask = 0u;
-#pragma unroll
-            for (int mx = 0; mx < 3; ++mx)
-#pragma unroll
-                for (int my = 0; my < 3; ++my)
-#pragma unroll
-                    for (int mz = 0; mz < 3; ++mz) {
-                        const float d2 = __fmaf_rd(gap[0][mx], gap[0][mx],
-                                                   __fmaf_rd(gap[1][my], gap[1][my],
-                                                             __fmul_rd(gap[2][mz], gap[2][mz])));
-                        if (d2 <= rs2) mask |= 1u << (mx * 9 + my * 3 + mz);
-                    }
+            const Frame f = frame_of(g);
+            unsigned mask = image_mask(me.x, me.y, me.z, L, g, rs2);
             const int root = g.count >= 2 ? g.start : ~g.start;
             const int last = g.start + g.count - 1;
             while (mask) {
                 const int img = __ffs(mask) - 1;
                 mask &= mask - 1u;
-                c.nx = img / 9 - 1;
-                c.ny = (img / 3) % 3 - 1;
-                c.nz = img % 3 - 1;
-                c.nLx = c.nx == 0 ? 0.f : (c.nx > 0 ? c.L : -c.L);
-                c.nLy = c.ny == 0 ? 0.f : (c.ny > 0 ? c.L : -c.L);
-                c.nLz = c.nz == 0 ? 0.f : (c.nz > 0 ? c.L : -c.L);
-                const float px = c.nx == 0 ? me.x : __fadd_rn(me.x, c.nLx);
-                const float py = c.ny == 0 ? me.y : __fadd_rn(me.y, c.nLy);
-                const float pz = c.nz == 0 ? me.z : __fadd_rn(me.z, c.nLz);
+                set_image(c, img, L);
                 int node = root;
-                // pre-order visits every node at most once: 2 count - 1 steps
-                int budget = 2 * g.count;
+                int budget = 2 * g.count;   // pre-order visits each node at most once
                 while (node != QBVH_END) {
-                    if (--budget < 0 || node > last || ~node > last || (node >= 0 && node < g.start) ||
-                        (node < 0 && ~node < g.start)) {
+                    if (--budget < 0 || bad_node(node, g, last)) {
                         atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
                         break;
                     }
                     if (node >= 0) {
-                        const int4 w = __ldg(a.nodes + node);
-                        if (overlap_q(px, py, pz, (unsigned)w.x, (unsigned)w.y, f, rs2)) {
-                            if (w.x < 0) {   // bundle: test its leaves directly
-                                int l = (w.w == QBVH_END) ? last : ((w.w >= 0 ? w.w : ~w.w) - 1);
-                                if (w.z < g.start || l > last) {
+                        const Node nd = decode<FMT>(load_raw<FMT>(a, node), f);
+                        if (overlap(c.px, c.py, c.pz, nd, rs2)) {
+                            if (nd.bundle) {
+                                int l = bundle_last(nd, last);
+                                if (nd.left < g.start || l > last) {
                                     atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
-                                    l = w.z - 1;
+                                    l = nd.left - 1;
                                 }
-                                for (int j = w.z; j <= l; ++j) {
-                                    const float4 q = __ldg(a.leaves + j);
-                                    if (CAND)
-                                        candidate_leaf(c, j, q, __ldg(leaf_q + j), f, px, py, pz, rs2);
-                                    else
-                                        exact_leaf(c, j, q);
-                                }
-                                node = w.w;
+                                for (int j = nd.left; j <= l; ++j)
+                                    test_leaf<CAND>(a, c, out, j, __ldg(a.leaves + j), f, rs2);
+                                node = nd.rope;
                             } else {
-                                node = w.z;
+                                node = nd.left;
                             }
                         } else {
-                            node = w.w;
+                            node = nd.rope;
                         }
                     } else {
                         const int j = ~node;
                         const float4 q = __ldg(a.leaves + j);
-                        if (CAND)
-                            candidate_leaf(c, j, q, __ldg(leaf_q + j), f, px, py, pz, rs2);
-                        else
-                            exact_leaf(c, j, q);
+                        test_leaf<CAND>(a, c, out, j, q, f, rs2);
                         node = (j == last) ? QBVH_END : ((__float_as_int(q.w) < 0) ? j + 1 : ~(j + 1));
                     }
                 }
             }
         }
-        a.counts[i_orig] = c.count;
-        my_count = c.count;
+        a.counts[i_orig] = out.count;
+        my_count = out.count;
     }
-    // largest row count of the block -> one atomic
-    int m = __reduce_max_sync(0xFFFFFFFFu, my_count);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_max[warp] = m;
-    __syncthreads();
-    if (warp == 0) {
-        m = (lane < (int)(blockDim.x >> 5)) ? s_max[lane] : 0;
-        m = __reduce_max_sync(0xFFFFFFFFu, m);
-        if (lane == 0 && m > 0) atomicMax(&a.status->max_count, m);
+    warp_max_count(my_count, a.status);
+}
+
+// ---- one warp per 32 consecutive Z-order particles ----------------------
+template <bool WIDE, bool CAND, int FMT>
+__global__ void query_warp_kernel(const __grid_constant__ QueryArgs a)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = s < a.n;
+    float4 me = make_float4(0.f, 0.f, 0.f, 0.f);
+    int i_orig = 0, seg_i = -1;
+    if (active) {
+        me = __ldg(a.leaves + s);
+        i_orig = __float_as_int(me.w) & 0x7FFFFFFF;
+        if (i_orig >= a.n) {
+            atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
+            i_orig = s;
+        }
+        seg_i = seg_of_sorted<WIDE>(a, s);
     }
+    Query c;
+    c.xi = me.x;
+    c.yi = me.y;
+    c.zi = me.z;
+    c.self = s;
+    Row out;
+    out.row = a.rows + (size_t)i_orig * a.cap;
+    out.cap = a.cap;
+    out.count = 0;
+    const int T = a.n_types;
+    // the warp's particles may belong to several trees (segment boundaries):
+    // take one segment value at a time
+    unsigned remaining = __ballot_sync(FULL, active);
+    while (remaining) {
+        const int seg = __shfl_sync(FULL, seg_i, __ffs(remaining) - 1);
+        const bool part = active && seg_i == seg;
+        remaining &= ~__ballot_sync(FULL, part);
+        const int sys = seg / T;
+        const int ta = seg - sys * T;
+        const float L = a.sys[sys].L;
+        for (int tb = 0; tb < T; ++tb) {
+            const float rl = a.r_list[ta * T + tb];
+            if (!(rl > 0.f)) continue;
+            const SegInfo g = a.seg[sys * T + tb];
+            if (g.count == 0) continue;
+            c.rl2 = a.rl2[ta * T + tb];
+            const float rs2 = a.rs2[ta * T + tb];
+            const Frame f = frame_of(g);
+            const unsigned mine = part ? image_mask(me.x, me.y, me.z, L, g, rs2) : 0u;
+            unsigned mask = __reduce_or_sync(FULL, mine);
+            const int root = g.count >= 2 ? g.start : ~g.start;
+            const int last = g.start + g.count - 1;
+            while (mask) {
+                const int img = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                set_image(c, img, L);
+                const bool on = (mine >> img) & 1u;
+                const float lrs2 = on ? rs2 : -1.f;   // a negative squared radius overlaps nothing
+                int node = root;
+                int budget = 2 * g.count;
+                while (node != QBVH_END) {
+                    if (--budget < 0 || bad_node(node, g, last)) {
+                        atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
+                        break;
+                    }
+                    if (node >= 0) {
+                        const Node nd = decode<FMT>(load_raw<FMT>(a, node), f);
+                        const bool hit = overlap(c.px, c.py, c.pz, nd, lrs2);
+                        if (__any_sync(FULL, hit)) {
+                            if (nd.bundle) {
+                                int l = bundle_last(nd, last);
+                                if (nd.left < g.start || l > last) {
+                                    atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
+                                    l = nd.left - 1;
+                                }
+                                for (int j = nd.left; j <= l; ++j) {
+                                    const float4 q = __ldg(a.leaves + j);
+                                    if (on) test_leaf<CAND>(a, c, out, j, q, f, rs2);
+                                }
+                                node = nd.rope;
+                            } else {
+                                node = nd.left;
+                            }
+                        } else {
+                            node = nd.rope;
+                        }
+                    } else {
+                        const int j = ~node;
+                        const float4 q = __ldg(a.leaves + j);
+                        if (on) test_leaf<CAND>(a, c, out, j, q, f, rs2);
+                        node = (j == last) ? QBVH_END : ((__float_as_int(q.w) < 0) ? j + 1 : ~(j + 1));
+                    }
+                }
+            }
+        }
+    }
+    if (active) a.counts[i_orig] = out.count;
+    warp_max_count(active ? out.count : 0, a.status);
 }
 
 }  // namespace
@@ -267,17 +464,24 @@ void launch_query(const QueryArgs &a, cudaStream_t s)
     if (a.n == 0) return;
     const int b = a.block;
     const int grid = (a.n + b - 1) / b;
-    if (a.wide_keys) {
-        if (a.candidates)
-            query_kernel<true, true><<<grid, b, 0, s>>>(a);
-        else
-            query_kernel<true, false><<<grid, b, 0, s>>>(a);
+#define QBVH_LAUNCH(K, F)                                                            \
+    do {                                                                             \
+        if (a.wide_keys) {                                                           \
+            if (a.candidates) K<true, true, F><<<grid, b, 0, s>>>(a);                \
+            else K<true, false, F><<<grid, b, 0, s>>>(a);                            \
+        } else {                                                                     \
+            if (a.candidates) K<false, true, F><<<grid, b, 0, s>>>(a);               \
+            else K<false, false, F><<<grid, b, 0, s>>>(a);                           \
+        }                                                                            \
+    } while (0)
+    if (a.traversal == 0) {
+        if (a.node_fmt == 0) QBVH_LAUNCH(query_thread_kernel, 0);
+        else QBVH_LAUNCH(query_thread_kernel, 1);
     } else {
-        if (a.candidates)
-            query_kernel<false, true><<<grid, b, 0, s>>>(a);
-        else
-            query_kernel<false, false><<<grid, b, 0, s>>>(a);
+        if (a.node_fmt == 0) QBVH_LAUNCH(query_warp_kernel, 0);
+        else QBVH_LAUNCH(query_warp_kernel, 1);
     }
+#undef QBVH_LAUNCH
 }
 
 }  // namespace qbvh

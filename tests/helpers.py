@@ -35,7 +35,8 @@ def assert_same_lists(rows_g, counts_g, rows_o, counts_o, idx=None):
         assert np.array_equal(a[:, :w], b[:, :w])
 
 
-def gpu_list(system, cap=256, bundle=None, block=None, candidates=None, max_retries=4):
+def gpu_list(system, cap=256, bundle=None, block=None, candidates=None, max_retries=4, traversal=None,
+             node_format=None):
     import torch
     from paper_1901_08088_gb300 import NeighborList, _lib
 
@@ -46,6 +47,10 @@ def gpu_list(system, cap=256, bundle=None, block=None, candidates=None, max_retr
         nl.set_option(_lib.QBVH_OPT_QUERY_BLOCK, block)
     if candidates is not None:
         nl.set_option(_lib.QBVH_OPT_CANDIDATES, candidates)
+    if traversal is not None:
+        nl.set_option(_lib.QBVH_OPT_TRAVERSAL, traversal)
+    if node_format is not None:
+        nl.set_option(_lib.QBVH_OPT_NODE_FORMAT, node_format)
     pos4 = torch.from_numpy(workloads.pack_float4(system.pos, system.types)).cuda()
     nl.build(pos4, system.L, system.n_types)
     nl.query(system.r_list, cap=cap, max_retries=max_retries)

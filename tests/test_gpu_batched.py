@@ -11,13 +11,15 @@ from helpers import assert_same_lists, concat, oracle_list
 pytestmark = pytest.mark.gpu
 
 
-def _batched(systems, n_types=1, cap=256, r=None):
+def _batched(systems, n_types=1, cap=256, r=None, traversal=None):
     import torch
 
-    from paper_1901_08088_gb300 import NeighborList
+    from paper_1901_08088_gb300 import NeighborList, _lib
 
     pos4, off, Ls = concat(systems)
     nl = NeighborList(0)
+    if traversal is not None:
+        nl.set_option(_lib.QBVH_OPT_TRAVERSAL, traversal)
     nl.build_batched(torch.from_numpy(pos4).cuda(), off, Ls, n_types=n_types)
     nl.query(systems[0].r_list if r is None else r, cap=cap)
     rows, counts = nl.neighbors()
@@ -32,9 +34,10 @@ def _check_systems(systems, rows, counts, off):
         assert_same_lists(rows[a:b] - a, counts[a:b], ro, co)
 
 
-def test_small_ensemble_matches_oracle_per_system():
+@pytest.mark.parametrize("traversal", [0, 1])
+def test_small_ensemble_matches_oracle_per_system(traversal):
     systems = workloads.batched_ensemble(seed=5, n_sys=12, n_min=250, n_max=3000)
-    rows, counts, off, nl = _batched(systems)
+    rows, counts, off, nl = _batched(systems, traversal=traversal)
     _check_systems(systems, rows, counts, off)
     nl.close()
 
@@ -84,9 +87,10 @@ def test_ensemble_with_empty_and_single_particle_systems():
     nl.close()
 
 
-def test_two_type_batched_systems():
+@pytest.mark.parametrize("traversal", [0, 1])
+def test_two_type_batched_systems(traversal):
     systems = workloads.two_type_lj(seed=8, n_sys=3, n=5000)
-    rows, counts, off, nl = _batched(systems, n_types=2)
+    rows, counts, off, nl = _batched(systems, n_types=2, traversal=traversal)
     _check_systems(systems, rows, counts, off)
     nl.close()
 

@@ -32,9 +32,13 @@ def _run(nl, s, pos4, E, S, rc, weights=None):
     return U.detach().cpu().numpy(), xyz.grad.cpu().numpy(), eps.grad.cpu().numpy(), sig.grad.cpu().numpy()
 
 
-def test_single_type_energy_forces():
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+def test_single_type_energy_forces(lanes):
+    from paper_1901_08088_gb300 import _lib
+
     s = workloads.workload("lj_n4096_rho0.6", seed=1)
     rg, cg, nl, pos4 = gpu_list(s)
+    nl.set_option(_lib.QBVH_OPT_LJ_LANES, lanes)
     U, gx, ge, gs = _run(nl, s, pos4, [[1.0]], [[1.0]], 3.0)
     ro, co = oracle_list(s, method="brute")
     ref = oracle.lj_fp64(s.pos, s.types, s.L, [[1.0]], [[1.0]], np.float32(3.0), ro, co)
@@ -45,10 +49,14 @@ def test_single_type_energy_forces():
     nl.close()
 
 
-def test_two_types_parameter_gradients_and_weighted_backward():
+@pytest.mark.parametrize("lanes", [1, 8, 32])
+def test_two_types_parameter_gradients_and_weighted_backward(lanes):
+    from paper_1901_08088_gb300 import _lib
+
     sys0 = workloads.two_type_lj(seed=2, n_sys=1, n=8000)[0]
     E, S = sys0.meta["eps"], sys0.meta["sig"]
     rg, cg, nl, pos4 = gpu_list(sys0)
+    nl.set_option(_lib.QBVH_OPT_LJ_LANES, lanes)
     U, gx, ge, gs = _run(nl, sys0, pos4, E, S, 2.5, weights=[-0.75])
     ro, co = oracle_list(sys0)
     ref = oracle.lj_fp64(sys0.pos, sys0.types, sys0.L, E, S, np.float32(2.5), ro, co)

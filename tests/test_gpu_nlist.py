@@ -19,9 +19,11 @@ def cfg1():
     return workloads.workload("lj_n4096_rho0.6", seed=0)
 
 
-@pytest.mark.parametrize("bundle,block", [(1, 128), (4, 128), (8, 64), (2, 256)])
-def test_config1_exact_list_equals_bruteforce(cfg1, bundle, block):
-    rg, cg, nl, _ = gpu_list(cfg1, bundle=bundle, block=block)
+@pytest.mark.parametrize("node_format", [0, 1])
+@pytest.mark.parametrize("traversal", [0, 1])
+@pytest.mark.parametrize("bundle,block", [(1, 128), (4, 128), (8, 64), (2, 256), (16, 128)])
+def test_config1_exact_list_equals_bruteforce(cfg1, bundle, block, traversal, node_format):
+    rg, cg, nl, _ = gpu_list(cfg1, bundle=bundle, block=block, traversal=traversal, node_format=node_format)
     ro, co = oracle_list(cfg1, method="brute")
     assert_same_lists(rg, cg, ro, co)
     assert nl.max_count == co.max()
@@ -54,11 +56,12 @@ def _uniform(n, L, r, seed, n_types=1):
                             r_cut=rl.copy())
 
 
+@pytest.mark.parametrize("traversal,node_format", [(0, 0), (1, 0), (1, 1)])
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 31, 33, 255, 4095, 4097, 12345])
-def test_ragged_sizes(n):
+def test_ragged_sizes(n, traversal, node_format):
     L = max(8.0, (n / 0.5) ** (1 / 3))
     s = _uniform(n, L, 2.5, seed=n)
-    rg, cg, nl, _ = gpu_list(s)
+    rg, cg, nl, _ = gpu_list(s, traversal=traversal, node_format=node_format)
     ro, co = oracle_list(s, method="brute")
     assert_same_lists(rg, cg, ro, co)
     nl.close()
@@ -98,10 +101,11 @@ def test_particles_on_both_faces_of_the_box():
     nl.close()
 
 
-def test_two_types_per_pair_cutoffs():
+@pytest.mark.parametrize("traversal", [0, 1])
+def test_two_types_per_pair_cutoffs(traversal):
     s = _uniform(20000, 30.0, 1.0, seed=5, n_types=3)
     s.r_list = np.array([[2.0, 2.5, 3.0], [2.5, 1.5, 0.0], [3.0, 0.0, 4.0]], np.float32)
-    rg, cg, nl, _ = gpu_list(s)
+    rg, cg, nl, _ = gpu_list(s, traversal=traversal)
     ro, co = oracle_list(s)
     assert_same_lists(rg, cg, ro, co)
     t = nl.tree()
@@ -147,6 +151,18 @@ def test_overflow_retry_and_truncation(cfg1):
     nl.close()
 
 
+def test_radius_close_to_half_box():
+    # the largest radius the library accepts: r just below (L/2)(1 - 2^-20)
+    L = np.float32(8.0)
+    r = np.float32(4.0 * (1 - 2.0 ** -19))
+    s = _uniform(3000, float(L), float(r), seed=11)
+    s.r_list[:] = r
+    rg, cg, nl, _ = gpu_list(s, cap=2048)
+    ro, co = oracle_list(s, cap=2048, method="brute")
+    assert_same_lists(rg, cg, ro, co)
+    nl.close()
+
+
 def test_invalid_inputs_report_errors():
     import torch
 
@@ -171,8 +187,9 @@ def test_invalid_inputs_report_errors():
     nl.close()
 
 
-def test_candidate_mode_is_a_superset_with_few_false_positives(cfg1):
-    rg, cg, nl, _ = gpu_list(cfg1, candidates=1, cap=512)
+@pytest.mark.parametrize("traversal", [0, 1])
+def test_candidate_mode_is_a_superset_with_few_false_positives(cfg1, traversal):
+    rg, cg, nl, _ = gpu_list(cfg1, candidates=1, cap=512, traversal=traversal)
     ro, co = oracle_list(cfg1, method="brute")
     sets_o = oracle.rows_as_sets(ro, co)
     sets_g = oracle.rows_as_sets(rg, cg)
@@ -207,9 +224,10 @@ def test_handle_reuse_across_sizes():
 
 
 @pytest.mark.slow
-def test_full_size_lj_2m():
+@pytest.mark.parametrize("traversal,node_format", [(0, 0), (1, 0), (1, 1)])
+def test_full_size_lj_2m(traversal, node_format):
     s = workloads.workload("lj_n2097152_rho0.8", seed=0)
-    rg, cg, nl, _ = gpu_list(s)
+    rg, cg, nl, _ = gpu_list(s, traversal=traversal, node_format=node_format)
     ro, co = oracle_list(s)
     rng = np.random.default_rng(0)
     idx = np.sort(rng.choice(s.n, 8192, replace=False))
