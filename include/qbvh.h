@@ -246,6 +246,37 @@ int qbvh_lj_backward(qbvh_handle h, const double *g_dev, const float *F_dev,
                      float *grad_eps_dev, float *grad_sig_dev, cudaStream_t stream);
 
 /*
+ * Allocation-free variant of qbvh_lj_forward, for callers that cannot allocate
+ * device memory when they need forces: an allocator locked for the length of
+ * a step, a plugin inside a host program that owns every device allocation,
+ * or a loop where cudaMalloc/cudaFree (which may synchronize the device) are
+ * not allowed.  The paper has no counterpart; this is an interface choice of
+ * this library.
+ *
+ * Same energies, forces and eps/sigma gradients as qbvh_lj_forward, for ONE
+ * periodic system of edge L and a neighbor list the caller passes in
+ * (rows_dev [n][cap], counts_dev [n], as nlist_get returns them); no handle.
+ * pos_dev, eps_dev, sig_dev, e_dev, F_dev: as for qbvh_lj_forward;
+ * r_cut_host: [n_types][n_types] float32 on the host; U_dev: [1] float64;
+ * dE_dev, dS_dev: [n_types][n_types] float64 (or NULL).
+ *
+ * Nothing is allocated: the per-block FP64 sums live in a fixed array of
+ * 1216 x 33 doubles (about 321 KB) inside the library, which every GPU that
+ * loads the library holds until the process exits.  Limit: n_types <= 4
+ * (larger counts return QBVH_ERR_INVALID_ARG because their sums would not fit
+ * that array).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, on the current device); make that first call
+ * before any stream capture.  Every call overwrites the parts of the array it
+ * reads, so no clearing is needed, but calls that overlap on the GPU (several
+ * streams or host threads) share the array and race.  Runs on the current
+ * device.  Errors: INVALID_ARG, CUDA.
+ */
+int qbvh_lj_forward_noalloc(const void *pos_dev, int n, float L, int n_types, const int *rows_dev,
+                            const int *counts_dev, int cap, const float *eps_dev, const float *sig_dev,
+                            const float *r_cut_host, float *e_dev, double *U_dev, float *F_dev,
+                            double *dE_dev, double *dS_dev, cudaStream_t stream);
+
+/*
  * Pack positions [n][3] float32 and types [n] int32 (types_dev may be NULL
  * for all-zero) into the float4 layout the build reads.
  */

@@ -21,7 +21,7 @@ __all__ = [
     "qbvh_create", "qbvh_destroy", "qbvh_set_option", "qbvh_get_option",
     "qbvh_build", "qbvh_build_batched", "qbvh_query", "qbvh_query_async", "qbvh_query_status",
     "nlist_get", "qbvh_tree_get", "qbvh_lj_forward", "qbvh_lj_backward", "qbvh_pack_positions",
-    "qbvh_strerror",
+    "qbvh_lj_forward_noalloc", "qbvh_strerror",
 ]
 
 
@@ -150,6 +150,17 @@ def qbvh_lj_forward(h: int, pos4, eps, sig, r_cut_host, e, U, F, dE, dS, stream=
 def qbvh_lj_backward(h: int, g, F, dE, dS, gpos, geps, gsig, stream=None) -> int:
     return lib().qbvh_lj_backward(h, _ptr(g), _ptr(F), _ptr(dE), _ptr(dS), _ptr(gpos), _ptr(geps),
                                   _ptr(gsig), _stream_ptr(stream))
+
+
+def qbvh_lj_forward_noalloc(pos4, L, n_types, rows, counts, eps, sig, r_cut_host, e, U, F, dE, dS,
+                            stream=None) -> int:
+    """Allocation-free LJ pass over a caller-provided list (one system)."""
+    rc = np.ascontiguousarray(np.asarray(r_cut_host, np.float32))
+    n = int(pos4.shape[0])
+    return lib().qbvh_lj_forward_noalloc(_ptr(pos4) if n else None, n, float(np.float32(L)), int(n_types),
+                                         _ptr(rows) if n else None, _ptr(counts) if n else None,
+                                         int(rows.shape[1]), _ptr(eps), _ptr(sig), rc.ctypes.data_as(C.c_void_p),
+                                         _ptr(e), _ptr(U), _ptr(F), _ptr(dE), _ptr(dS), _stream_ptr(stream))
 
 
 def qbvh_pack_positions(xyz: torch.Tensor, types, out4: torch.Tensor, stream=None) -> int:
