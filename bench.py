@@ -110,7 +110,7 @@ def run_ours(args):
     import torch.distributed as dist
 
     import workloads
-    from paper_1901_08088_gb300 import NeighborList, _lib
+    from paper_1901_08088_gb300 import NeighborList, _lib, autotune
     from paper_1901_08088_gb300.qbvh import qbvh_lj_forward, check
 
     world, rank, local = _dist()
@@ -126,16 +126,6 @@ def run_ours(args):
     pos4_host = torch.from_numpy(workloads.pack_float4(s.pos, s.types)).pin_memory()
     pos4 = pos4_host.cuda()
     nl = NeighborList(local)
-    if args.bundle:
-        nl.set_option(_lib.QBVH_OPT_BUNDLE, args.bundle)
-    if args.block:
-        nl.set_option(_lib.QBVH_OPT_QUERY_BLOCK, args.block)
-    if args.traversal >= 0:
-        nl.set_option(_lib.QBVH_OPT_TRAVERSAL, args.traversal)
-    if args.node_format >= 0:
-        nl.set_option(_lib.QBVH_OPT_NODE_FORMAT, args.node_format)
-    if args.lj_lanes:
-        nl.set_option(_lib.QBVH_OPT_LJ_LANES, args.lj_lanes)
     eps = torch.ones((1, 1), dtype=torch.float32, device="cuda")
     sig = torch.ones((1, 1), dtype=torch.float32, device="cuda")
     U = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -147,6 +137,31 @@ def run_ours(args):
         nl.build(p4, s.L)
         nl.query(s.r_list, cap=CAP)
         check(qbvh_lj_forward(nl.h, p4, eps, sig, rc, None, U, F, None, None), "lj")
+
+    # options: explicit flags win; otherwise the autotuner picks them during
+    # warm-up (the paper tunes launch parameters at run time, then freezes them)
+    explicit = {}
+    if args.bundle:
+        explicit[_lib.QBVH_OPT_BUNDLE] = args.bundle
+    if args.block:
+        explicit[_lib.QBVH_OPT_QUERY_BLOCK] = args.block
+    if args.traversal >= 0:
+        explicit[_lib.QBVH_OPT_TRAVERSAL] = args.traversal
+    if args.node_format >= 0:
+        explicit[_lib.QBVH_OPT_NODE_FORMAT] = args.node_format
+    if args.lj_lanes:
+        explicit[_lib.QBVH_OPT_LJ_LANES] = args.lj_lanes
+    tuned, tune_evals = dict(explicit), 0
+    if not args.no_autotune:
+        def tune_step(opts):
+            for k, v in opts.items():
+                nl.set_option(k, v)
+            step(pos4)
+        space = {k: v for k, v in autotune.OPTION_SPACE.items() if k not in explicit}
+        tuned, _, log = autotune.tune(tune_step, space=space, start=explicit, reps=3, warmup=1, sweeps=2)
+        tune_evals = len(log)
+    for k, v in tuned.items():
+        nl.set_option(k, v)
 
     for _ in range(args.warmup):
         step(pos4)
@@ -263,11 +278,15 @@ def run_ours(args):
             "e2e": {"value": world * n * e2e_steps / (e2e_ms * 1e-3), "unit": "particles/s",
                     "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 12 * n + 8},
             "gpu_launches": args.steps * 14,
+            "autotune": {"evaluations": tune_evals, "chosen": autotune.option_names(
+                {k: nl.get_option(k) for k in autotune.OPTION_SPACE})},
             "clocks": clocks,
             "wall_s_timed": wall,
         }
         if args.n:
             out["config"]["workload"] = f"profiling case: LJ fluid N={n} rho=0.8 (not a bench result)"
+        if not args.no_batched and world == 1:
+            out["batched"] = run_batched(args, local)
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(s, samples=1)
         elif world == 1:
@@ -277,6 +296,70 @@ def run_ours(args):
         dist.barrier()
         dist.destroy_process_group()
     return out
+
+
+def run_batched(args, local):
+    """256 independent systems: batched build+query from one CUDA graph vs the per-system loop."""
+    import torch
+
+    import workloads
+    from paper_1901_08088_gb300 import BatchedNeighborList, PerSystemLoop, _lib, autotune
+
+    systems = workloads.workload("ensemble_256", seed=0)
+    pos4 = np.concatenate([workloads.pack_float4(x.pos, x.types) for x in systems])
+    off = np.concatenate([[0], np.cumsum([x.n for x in systems])]).astype(np.int32)
+    Ls = np.array([x.L for x in systems], np.float32)
+    total = int(off[-1])
+    buf = torch.from_numpy(pos4).cuda()
+    r = systems[0].r_list
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    runners = {}
+
+    def graph_step(opts):
+        key = tuple(sorted(opts.items()))
+        if key not in runners:
+            runners[key] = BatchedNeighborList(buf, off, Ls, r, cap=128, options=opts, device=local).capture()
+        g = runners[key]
+        g.replay()
+
+    space = {k: autotune.OPTION_SPACE[k] for k in (_lib.QBVH_OPT_BUNDLE, _lib.QBVH_OPT_NODE_FORMAT,
+                                                   _lib.QBVH_OPT_QUERY_BLOCK)}
+    best, _, _ = autotune.tune(graph_step, space=space, reps=3, warmup=1, sweeps=1)
+    g = runners[tuple(sorted(best.items()))]
+    for x in runners.values():
+        if x is not g:
+            x.close()
+    for _ in range(3):
+        assert g.run() == _lib.QBVH_OK
+    reps = max(args.steps, 5)
+    graph_ms = timed(lambda: (g.replay(), stream.synchronize(), g.status()), reps)
+    loop = PerSystemLoop(buf, off, Ls, r, cap=g.cap, options=best, device=local)
+    for _ in range(2):
+        assert loop.run() == _lib.QBVH_OK
+    loop_ms = timed(lambda: loop.run(), reps)
+    loop.close()
+    g.close()
+    return {
+        "workload": f"{len(systems)} LJ systems, N log-uniform [500, 50000] (sum N = {total}), "
+                    "rho U[0.3, 0.9], jitter 0.3, r_list = 2.8; build + query per step",
+        "graph_particles_per_s": total / (graph_ms * 1e-3),
+        "loop_particles_per_s": total / (loop_ms * 1e-3),
+        "graph_ms": graph_ms, "loop_ms": loop_ms, "ratio": loop_ms / graph_ms,
+        "options": autotune.option_names(best),
+    }
 
 
 def cpu_baseline(s, samples=1):
@@ -331,10 +414,12 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-system graph-vs-loop measurement")
     ap.add_argument("--n", type=int, default=0,
                     help="profiling aid: run the same fluid with N particles instead of 2,097,152 "
                          "(the line it prints is not a bench result)")

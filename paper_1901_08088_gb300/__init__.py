@@ -8,3 +8,5 @@ from ._lib import QBVHError, LIB_PATH  # noqa: F401
 from .qbvh import *  # noqa: F401,F403
 from .qbvh import NeighborList  # noqa: F401
 from .lj import LJEnergy, lj_energy, pack_positions  # noqa: F401
+from .batch import BatchedNeighborList, PerSystemLoop  # noqa: F401
+from . import autotune  # noqa: F401

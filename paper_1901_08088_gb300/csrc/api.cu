@@ -16,7 +16,7 @@
 using namespace qbvh;
 
 namespace qbvh {
-int lj_block_size();
+int lj_particles_per_block();
 }
 
 namespace {
@@ -72,7 +72,6 @@ struct qbvh_ctx {
     DevBuf rows, counts;
     DevBuf lj_partials, lj_blk_sys, lj_blk_first, lj_sys_blk;
     std::vector<int> lj_layout_off;   // offsets the LJ block tables were built for
-    int lj_layout_tpp = 0;
     int lj_n_blocks = 0;
     // uploads cached by content
     std::vector<SysInfo> up_sys;
@@ -555,9 +554,9 @@ int qbvh_lj_forward(qbvh_handle h, const void *pos_dev, const float *eps_dev, co
     }
     DeviceGuard g(h->device);
     // block tables: every block covers particles of one system
-    const int B = lj_block_size() / h->lj_tpp;   // particles per block
+    const int B = lj_particles_per_block();
     int rc = QBVH_OK;
-    if (h->lj_layout_off != h->off || h->lj_layout_tpp != h->lj_tpp || h->lj_blk_sys.p == nullptr) {
+    if (h->lj_layout_off != h->off || h->lj_blk_sys.p == nullptr) {
         std::vector<int> blk_sys, blk_first, sys_blk(h->n_sys + 1, 0);
         for (int k = 0; k < h->n_sys; ++k) {
             sys_blk[k] = (int)blk_sys.size();
@@ -582,7 +581,6 @@ int qbvh_lj_forward(qbvh_handle h, const void *pos_dev, const float *eps_dev, co
             cudaMemcpyAsync(h->lj_sys_blk.p, sys_blk.data(), sys_blk.size() * 4, cudaMemcpyHostToDevice, stream))
             return QBVH_ERR_CUDA;
         h->lj_layout_off = h->off;
-        h->lj_layout_tpp = h->lj_tpp;
     }
     const int np = 1 + 2 * T * T;
     rc = ensure(h, h->lj_partials, (size_t)(h->lj_n_blocks > 0 ? h->lj_n_blocks : 1) * np * 8);

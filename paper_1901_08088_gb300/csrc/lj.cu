@@ -21,6 +21,7 @@ namespace qbvh {
 namespace {
 
 constexpr int kLJBlock = 128;
+constexpr int kLJParticles = 256;   // particles per block, taken in rounds of kLJBlock / TPP
 
 __device__ __forceinline__ float mi_component(float d, float L, float Linv)
 {
@@ -51,80 +52,83 @@ __global__ void __launch_bounds__(kLJBlock) lj_forward_kernel(const __grid_const
     const int sys = a.blk_sys[blockIdx.x];
     const SysInfo sy = a.sys[sys];
     const int sub = tid % TPP;
-    const int i = a.blk_first[blockIdx.x] + tid / TPP;
-    const bool active = i < sy.offset + sy.count;
-    float e = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
-    float gE[T], gS[T];
+    const int end = min(a.blk_first[blockIdx.x] + kLJParticles, sy.offset + sy.count);
+    double v[NP];
 #pragma unroll
-    for (int b = 0; b < T; ++b) gE[b] = gS[b] = 0.f;
-    int ta = 0;
-    if (active) {
-        const float4 pi = __ldg(a.pos + i);
-        ta = T > 1 ? __float_as_int(pi.w) : 0;
-        ta = ta < 0 ? 0 : (ta >= T ? T - 1 : ta);
-        const int c = min(__ldg(a.counts + i), a.cap);
-        const int *row = a.rows + (size_t)i * a.cap;
-        for (int k = sub; k < c; k += TPP) {
-            const int j = __ldg(row + k);
-            if ((unsigned)j >= (unsigned)a.n) continue;   // never for a list from the traversal
-            const float4 pj = __ldg(a.pos + j);
-            int tb = T > 1 ? __float_as_int(pj.w) : 0;
-            tb = tb < 0 ? 0 : (tb >= T ? T - 1 : tb);
-            const int p = ta * T + tb;
-            const float dx = mi_component(__fsub_rn(pj.x, pi.x), sy.L, sy.Linv);
-            const float dy = mi_component(__fsub_rn(pj.y, pi.y), sy.L, sy.Linv);
-            const float dz = mi_component(__fsub_rn(pj.z, pi.z), sy.L, sy.Linv);
-            const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-            if (!(r2 < s_rc2[p])) continue;
-            const float inv_r2 = __frcp_rn(r2);
-            const float s2 = s_sig2[p] * inv_r2;
-            const float s6 = s2 * s2 * s2;
-            const float uE = 4.f * (s6 * s6 - s6) - s_phic[p];   // u / eps
-            const float q = 2.f * s6 * s6 - s6;
-            const float w = 24.f * s_eps[p] * q * inv_r2;
-            e += s_eps[p] * uE;
-            fx -= w * dx;
-            fy -= w * dy;
-            fz -= w * dz;
+    for (int q = 0; q < NP; ++q) v[q] = 0.0;
+    for (int base = a.blk_first[blockIdx.x]; base < end; base += kLJBlock / TPP) {
+        const int i = base + tid / TPP;
+        const bool active = i < end;
+        float e = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+        float gE[T], gS[T];
 #pragma unroll
-            for (int b = 0; b < T; ++b) {
-                if (b == tb) {
-                    gE[b] += uE;
-                    gS[b] += (24.f * s_eps[p] / s_sig[p]) * (q - s_dsc[p]);
+        for (int b = 0; b < T; ++b) gE[b] = gS[b] = 0.f;
+        int ta = 0;
+        if (active) {
+            const float4 pi = __ldg(a.pos + i);
+            ta = T > 1 ? __float_as_int(pi.w) : 0;
+            ta = ta < 0 ? 0 : (ta >= T ? T - 1 : ta);
+            const int c = min(__ldg(a.counts + i), a.cap);
+            const int *row = a.rows + (size_t)i * a.cap;
+            for (int k = sub; k < c; k += TPP) {
+                const int j = __ldg(row + k);
+                if ((unsigned)j >= (unsigned)a.n) continue;   // never for a list from the traversal
+                const float4 pj = __ldg(a.pos + j);
+                int tb = T > 1 ? __float_as_int(pj.w) : 0;
+                tb = tb < 0 ? 0 : (tb >= T ? T - 1 : tb);
+                const int p = ta * T + tb;
+                const float dx = mi_component(__fsub_rn(pj.x, pi.x), sy.L, sy.Linv);
+                const float dy = mi_component(__fsub_rn(pj.y, pi.y), sy.L, sy.Linv);
+                const float dz = mi_component(__fsub_rn(pj.z, pi.z), sy.L, sy.Linv);
+                const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                if (!(r2 < s_rc2[p])) continue;
+                const float inv_r2 = __frcp_rn(r2);
+                const float s2 = s_sig2[p] * inv_r2;
+                const float s6 = s2 * s2 * s2;
+                const float uE = 4.f * (s6 * s6 - s6) - s_phic[p];   // u / eps
+                const float q = 2.f * s6 * s6 - s6;
+                const float w = 24.f * s_eps[p] * q * inv_r2;
+                e += s_eps[p] * uE;
+                fx -= w * dx;
+                fy -= w * dy;
+                fz -= w * dz;
+#pragma unroll
+                for (int b = 0; b < T; ++b) {
+                    if (b == tb) {
+                        gE[b] += uE;
+                        gS[b] += (24.f * s_eps[p] / s_sig[p]) * (q - s_dsc[p]);
+                    }
                 }
             }
         }
-    }
-    // per-particle results: FP32 sums over the group's lanes
-    float ei = e, fxi = fx, fyi = fy, fzi = fz;
+        // per-particle results: FP32 sums over the group's lanes
+        float ei = e, fxi = fx, fyi = fy, fzi = fz;
 #pragma unroll
-    for (int o = TPP / 2; o > 0; o >>= 1) {
-        ei += __shfl_xor_sync(0xFFFFFFFFu, ei, o);
-        fxi += __shfl_xor_sync(0xFFFFFFFFu, fxi, o);
-        fyi += __shfl_xor_sync(0xFFFFFFFFu, fyi, o);
-        fzi += __shfl_xor_sync(0xFFFFFFFFu, fzi, o);
-    }
-    if (active && sub == 0) {
-        if (a.e) a.e[i] = 0.5f * ei;
-        if (a.F) {
-            a.F[3 * (size_t)i] = fxi;
-            a.F[3 * (size_t)i + 1] = fyi;
-            a.F[3 * (size_t)i + 2] = fzi;
+        for (int o = TPP / 2; o > 0; o >>= 1) {
+            ei += __shfl_xor_sync(0xFFFFFFFFu, ei, o);
+            fxi += __shfl_xor_sync(0xFFFFFFFFu, fxi, o);
+            fyi += __shfl_xor_sync(0xFFFFFFFFu, fyi, o);
+            fzi += __shfl_xor_sync(0xFFFFFFFFu, fzi, o);
         }
-    }
-    // FP64 block reduction of the energy and the parameter-gradient terms
-    double v[NP];
-    v[0] = 0.5 * (double)e;
+        if (active && sub == 0) {
+            if (a.e) a.e[i] = 0.5f * ei;
+            if (a.F) {
+                a.F[3 * (size_t)i] = fxi;
+                a.F[3 * (size_t)i + 1] = fyi;
+                a.F[3 * (size_t)i + 2] = fzi;
+            }
+        }
+        // FP64 accumulation of the energy and the parameter-gradient terms
+        v[0] += 0.5 * (double)e;
+        if (active) {
 #pragma unroll
-    for (int q = 1; q < NP; ++q) v[q] = 0.0;
-    if (active) {
+            for (int b = 0; b < T; ++b) {
 #pragma unroll
-        for (int b = 0; b < T; ++b) {
-#pragma unroll
-            for (int t = 0; t < T; ++t) {
-                if (t == ta) {
-                    v[1 + t * T + b] = 0.5 * (double)gE[b];
-                    v[1 + T * T + t * T + b] = 0.5 * (double)gS[b];
+                for (int t = 0; t < T; ++t) {
+                    if (t == ta) {
+                        v[1 + t * T + b] += 0.5 * (double)gE[b];
+                        v[1 + T * T + t * T + b] += 0.5 * (double)gS[b];
+                    }
                 }
             }
         }
@@ -208,7 +212,7 @@ __global__ void pack_kernel(const float *xyz, const int *types, int n, float4 *o
 
 }  // namespace
 
-int lj_block_size() { return kLJBlock; }
+int lj_particles_per_block() { return kLJParticles; }
 
 template <int T>
 static void launch_lj_t(const LJArgs &a, cudaStream_t s)
