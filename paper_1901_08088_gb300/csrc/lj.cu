@@ -22,6 +22,10 @@ namespace {
 
 constexpr int kLJBlock = 128;
 constexpr int kLJParticles = 256;   // particles per block, taken in rounds of kLJBlock / TPP
+#ifndef QBVH_LJ_UNROLL
+#define QBVH_LJ_UNROLL 4
+#endif
+constexpr int kLJUnroll = QBVH_LJ_UNROLL;   // row entries per lane in flight
 
 __device__ __forceinline__ float mi_component(float d, float L, float Linv)
 {
@@ -70,33 +74,48 @@ __global__ void __launch_bounds__(kLJBlock) lj_forward_kernel(const __grid_const
             ta = ta < 0 ? 0 : (ta >= T ? T - 1 : ta);
             const int c = min(__ldg(a.counts + i), a.cap);
             const int *row = a.rows + (size_t)i * a.cap;
-            for (int k = sub; k < c; k += TPP) {
-                const int j = __ldg(row + k);
-                if ((unsigned)j >= (unsigned)a.n) continue;   // never for a list from the traversal
-                const float4 pj = __ldg(a.pos + j);
-                int tb = T > 1 ? __float_as_int(pj.w) : 0;
-                tb = tb < 0 ? 0 : (tb >= T ? T - 1 : tb);
-                const int p = ta * T + tb;
-                const float dx = mi_component(__fsub_rn(pj.x, pi.x), sy.L, sy.Linv);
-                const float dy = mi_component(__fsub_rn(pj.y, pi.y), sy.L, sy.Linv);
-                const float dz = mi_component(__fsub_rn(pj.z, pi.z), sy.L, sy.Linv);
-                const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-                if (!(r2 < s_rc2[p])) continue;
-                const float inv_r2 = __frcp_rn(r2);
-                const float s2 = s_sig2[p] * inv_r2;
-                const float s6 = s2 * s2 * s2;
-                const float uE = 4.f * (s6 * s6 - s6) - s_phic[p];   // u / eps
-                const float q = 2.f * s6 * s6 - s6;
-                const float w = 24.f * s_eps[p] * q * inv_r2;
-                e += s_eps[p] * uE;
-                fx -= w * dx;
-                fy -= w * dy;
-                fz -= w * dz;
+            // U row entries per lane are loaded before their positions, and all U
+            // positions before any arithmetic, to keep several loads in flight
+            for (int k0 = sub; k0 < c; k0 += TPP * kLJUnroll) {
+                int jj[kLJUnroll];
+                float4 pp[kLJUnroll];
 #pragma unroll
-                for (int b = 0; b < T; ++b) {
-                    if (b == tb) {
-                        gE[b] += uE;
-                        gS[b] += (24.f * s_eps[p] / s_sig[p]) * (q - s_dsc[p]);
+                for (int u = 0; u < kLJUnroll; ++u) {
+                    const int k = k0 + u * TPP;
+                    jj[u] = k < c ? __ldg(row + k) : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < kLJUnroll; ++u)
+                    if ((unsigned)jj[u] < (unsigned)a.n) pp[u] = __ldg(a.pos + jj[u]);
+#pragma unroll
+                for (int u = 0; u < kLJUnroll; ++u) {
+                    if ((unsigned)jj[u] >= (unsigned)a.n) continue;   // past the row end
+                    const float4 pj = pp[u];
+                    int tb = T > 1 ? __float_as_int(pj.w) : 0;
+                    tb = tb < 0 ? 0 : (tb >= T ? T - 1 : tb);
+                    const int p = ta * T + tb;
+                    const float dx = mi_component(__fsub_rn(pj.x, pi.x), sy.L, sy.Linv);
+                    const float dy = mi_component(__fsub_rn(pj.y, pi.y), sy.L, sy.Linv);
+                    const float dz = mi_component(__fsub_rn(pj.z, pi.z), sy.L, sy.Linv);
+                    const float r2 =
+                        __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                    if (!(r2 < s_rc2[p])) continue;
+                    const float inv_r2 = __frcp_rn(r2);
+                    const float s2 = s_sig2[p] * inv_r2;
+                    const float s6 = s2 * s2 * s2;
+                    const float uE = 4.f * (s6 * s6 - s6) - s_phic[p];   // u / eps
+                    const float q = 2.f * s6 * s6 - s6;
+                    const float w = 24.f * s_eps[p] * q * inv_r2;
+                    e += s_eps[p] * uE;
+                    fx -= w * dx;
+                    fy -= w * dy;
+                    fz -= w * dz;
+#pragma unroll
+                    for (int b = 0; b < T; ++b) {
+                        if (b == tb) {
+                            gE[b] += uE;
+                            gS[b] += (24.f * s_eps[p] / s_sig[p]) * (q - s_dsc[p]);
+                        }
                     }
                 }
             }

@@ -147,9 +147,11 @@ __device__ __forceinline__ bool overlap_q(float px, float py, float pz, uint2 q,
     return overlap(px, py, pz, n, rs2);
 }
 
-// Row writer.  Entries past cap are counted, not written.  (Gathering four
-// entries into one 16-byte store was measured slower: the extra selects and
-// registers cost more than the narrower stores.)
+// Row writer.  Entries past cap are counted, not written.  The list is never
+// read back by the traversal, so it is stored with the streaming (evict-first)
+// hint and does not push the tree out of L2.  (Gathering four entries into
+// one 16-byte store was measured slower: the extra selects and registers cost
+// more than the narrower stores.)
 struct Row {
     int *row;
     int cap;
@@ -157,7 +159,7 @@ struct Row {
 
     __device__ __forceinline__ void push(int j)
     {
-        if (count < cap) row[count] = j;
+        if (count < cap) __stcs(row + count, j);
         ++count;
     }
 };
@@ -171,11 +173,18 @@ struct Query {
 };
 
 // The exact test of leaf j under the current image (see the header comment).
+// SHIFT = false is the zero image, where subtracting n L = 0 is the identity.
+template <bool SHIFT>
 __device__ __forceinline__ void exact_leaf(const Query &c, Row &out, int j, const float4 q)
 {
-    const float dx = __fsub_rn(__fsub_rn(q.x, c.xi), c.nLx);
-    const float dy = __fsub_rn(__fsub_rn(q.y, c.yi), c.nLy);
-    const float dz = __fsub_rn(__fsub_rn(q.z, c.zi), c.nLz);
+    float dx = __fsub_rn(q.x, c.xi);
+    float dy = __fsub_rn(q.y, c.yi);
+    float dz = __fsub_rn(q.z, c.zi);
+    if (SHIFT) {
+        dx = __fsub_rn(dx, c.nLx);
+        dy = __fsub_rn(dy, c.nLy);
+        dz = __fsub_rn(dz, c.nLz);
+    }
     const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
     if (d2 < c.rl2 && j != c.self) out.push(__float_as_int(q.w) & 0x7FFFFFFF);
 }
@@ -188,14 +197,14 @@ __device__ __forceinline__ void candidate_leaf(const Query &c, Row &out, int j, 
     if (j != c.self && overlap_q(c.px, c.py, c.pz, lq, f, rs2)) out.push(__float_as_int(q.w) & 0x7FFFFFFF);
 }
 
-template <bool CAND>
+template <bool CAND, bool SHIFT = true>
 __device__ __forceinline__ void test_leaf(const QueryArgs &A, const Query &c, Row &out, int j, const float4 q,
                                           const Frame &f, float rs2)
 {
     if (CAND)
         candidate_leaf(c, out, j, q, __ldg(A.leaf_q + j), f, rs2);
     else
-        exact_leaf(c, out, j, q);
+        exact_leaf<SHIFT>(c, out, j, q);
 }
 
 // 27-bit set of the periodic images whose padded search sphere overlaps the
@@ -361,8 +370,63 @@ __global__ void query_thread_kernel(const __grid_constant__ QueryArgs a)
 }
 
 // ---- one warp per 32 consecutive Z-order particles ----------------------
+// The warp-uniform rope walk of one tree under one periodic image.
+template <bool CAND, int FMT, bool SHIFT>
+__device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Row &out, const SegInfo &g,
+                                          const Frame &f, int root, int last, bool on, float rs2)
+{
+    const float lrs2 = on ? rs2 : -1.f;   // a negative squared radius overlaps nothing
+    int node = root;
+    int budget = 2 * g.count;
+    while (node != QBVH_END) {
+        if (--budget < 0 || bad_node(node, g, last)) {
+            atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
+            break;
+        }
+        if (node >= 0) {
+            const Node nd = decode<FMT>(load_raw<FMT>(a, node), f);
+            const bool hit = overlap(c.px, c.py, c.pz, nd, lrs2);
+            if (__any_sync(FULL, hit)) {
+                if (nd.bundle) {
+                    int l = bundle_last(nd, last);
+                    if (nd.left < g.start || l > last) {
+                        atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
+                        l = nd.left - 1;
+                    }
+                    for (int j = nd.left; j <= l; ++j) {
+                        const float4 q = __ldg(a.leaves + j);
+                        if (on) test_leaf<CAND, SHIFT>(a, c, out, j, q, f, rs2);
+                    }
+                    node = nd.rope;
+                } else {
+                    node = nd.left;
+                }
+            } else {
+                node = nd.rope;
+            }
+        } else {
+            const int j = ~node;
+            const float4 q = __ldg(a.leaves + j);
+            if (on) test_leaf<CAND, SHIFT>(a, c, out, j, q, f, rs2);
+            node = (j == last) ? QBVH_END : ((__float_as_int(q.w) < 0) ? j + 1 : ~(j + 1));
+        }
+    }
+}
+
+// Registers are capped so that 8 blocks of 256 threads (64 warps) fit on an
+// SM: the walk is latency-bound and more resident warps hide more of it
+// (measured 2.37 -> 2.23 ms at N = 2M despite a few spilled bytes).
+#ifndef QBVH_QUERY_MIN_BLOCKS
+#define QBVH_QUERY_MIN_BLOCKS 8
+#endif
+#if QBVH_QUERY_MIN_BLOCKS > 0
+#define QBVH_QUERY_BOUNDS __launch_bounds__(256, QBVH_QUERY_MIN_BLOCKS)
+#else
+#define QBVH_QUERY_BOUNDS
+#endif
+
 template <bool WIDE, bool CAND, int FMT>
-__global__ void query_warp_kernel(const __grid_constant__ QueryArgs a)
+__global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ QueryArgs a)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = s < a.n;
@@ -414,42 +478,10 @@ __global__ void query_warp_kernel(const __grid_constant__ QueryArgs a)
                 mask &= mask - 1u;
                 set_image(c, img, L);
                 const bool on = (mine >> img) & 1u;
-                const float lrs2 = on ? rs2 : -1.f;   // a negative squared radius overlaps nothing
-                int node = root;
-                int budget = 2 * g.count;
-                while (node != QBVH_END) {
-                    if (--budget < 0 || bad_node(node, g, last)) {
-                        atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
-                        break;
-                    }
-                    if (node >= 0) {
-                        const Node nd = decode<FMT>(load_raw<FMT>(a, node), f);
-                        const bool hit = overlap(c.px, c.py, c.pz, nd, lrs2);
-                        if (__any_sync(FULL, hit)) {
-                            if (nd.bundle) {
-                                int l = bundle_last(nd, last);
-                                if (nd.left < g.start || l > last) {
-                                    atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
-                                    l = nd.left - 1;
-                                }
-                                for (int j = nd.left; j <= l; ++j) {
-                                    const float4 q = __ldg(a.leaves + j);
-                                    if (on) test_leaf<CAND>(a, c, out, j, q, f, rs2);
-                                }
-                                node = nd.rope;
-                            } else {
-                                node = nd.left;
-                            }
-                        } else {
-                            node = nd.rope;
-                        }
-                    } else {
-                        const int j = ~node;
-                        const float4 q = __ldg(a.leaves + j);
-                        if (on) test_leaf<CAND>(a, c, out, j, q, f, rs2);
-                        node = (j == last) ? QBVH_END : ((__float_as_int(q.w) < 0) ? j + 1 : ~(j + 1));
-                    }
-                }
+                if (img == 13)
+                    warp_walk<CAND, FMT, false>(a, c, out, g, f, root, last, on, rs2);
+                else
+                    warp_walk<CAND, FMT, true>(a, c, out, g, f, root, last, on, rs2);
             }
         }
     }
