@@ -127,6 +127,21 @@ def _profiled_traffic(opts: dict, n: int):
     return want["bytes"]
 
 
+def max_over_ranks(x: float) -> float:
+    """Largest value of x over the ranks of the default process group (x itself
+    without one).  The tensor lives where the backend needs it: CUDA for NCCL,
+    CPU for gloo."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _alg_bytes(n: int, total_neighbors: int) -> int:
     # positions read once (16 B), counts written (4 B), list entries written (4 B each)
     return 16 * n + 4 * n + 4 * int(total_neighbors)
@@ -225,11 +240,7 @@ def run_ours(args):
     t_query = np.array([ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)])
     t_lj = np.array([ev[k][2].elapsed_time(ev[k][3]) for k in range(args.steps)])
     t_step = t_build + t_query + t_lj
-    total_ms = float(t_step.sum())
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(float(t_step.sum()))
 
     # end-to-end through the public API with host buffers: H2D positions,
     # build + query + LJ, D2H forces and energy, every step
@@ -250,10 +261,7 @@ def run_ours(args):
         ee1.record(stream)
         ee1.synchronize()
         e2e_ms += ee0.elapsed_time(ee1)
-    if world > 1:
-        tt = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e2e_ms)
 
     out = None
     if rank == 0:

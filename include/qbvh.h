@@ -277,6 +277,18 @@ int qbvh_lj_forward_noalloc(const void *pos_dev, int n, float L, int n_types, co
                             double *dE_dev, double *dS_dev, cudaStream_t stream);
 
 /*
+ * Self-test of the bounded device-side waits (failure detection without a
+ * GPU fault).  Runs one tile of a radix-sort pass (the decoupled look-back of
+ * the Morton-code sort, Sec. 3) whose predecessor never publishes its counts,
+ * with a short poll limit (4096 polls).  The kernel gives up, records the
+ * timeout in its error word and finishes with every access in bounds; the
+ * expected return value is QBVH_ERR_DEVICE_TIMEOUT (QBVH_OK would mean the
+ * wait did not give up).  Allocates and frees about 50 KB on `device`;
+ * synchronizes `stream`.
+ */
+int qbvh_selftest_wait_timeout(int device, cudaStream_t stream);
+
+/*
  * Pack positions [n][3] float32 and types [n] int32 (types_dev may be NULL
  * for all-zero) into the float4 layout the build reads.
  */

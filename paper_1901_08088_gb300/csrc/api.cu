@@ -627,6 +627,25 @@ int qbvh_lj_backward(qbvh_handle h, const double *g_dev, const float *F_dev, con
     return cuda_status();
 }
 
+int qbvh_selftest_wait_timeout(int device, cudaStream_t stream)
+{
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return QBVH_ERR_CUDA;
+    }
+    DeviceGuard g(device);
+    unsigned *err = nullptr;
+    if (cudaMallocHost(&err, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return QBVH_ERR_OOM;
+    }
+    *err = 0u;
+    int rc = sort_wait_selftest(4096, err, stream) == 0 ? map_dev_err(*err) : QBVH_ERR_CUDA;
+    cudaFreeHost(err);
+    return rc;
+}
+
 int qbvh_pack_positions(const float *xyz_dev, const int *types_dev, int n, void *pos4_dev, cudaStream_t stream)
 {
     if (n < 0) return QBVH_ERR_INVALID_ARG;

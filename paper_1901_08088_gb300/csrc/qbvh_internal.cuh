@@ -114,6 +114,7 @@ size_t sort_scratch_bytes(int n, int passes);
 // of the buffer pair holding the result: 0 -> (keys_a, vals_a), 1 -> (keys_b, vals_b).
 int radix_sort_pairs(bool wide, void *keys_a, void *keys_b, int *vals_a, int *vals_b, int n,
                      int bits, void *scratch, unsigned *err, cudaStream_t s);
+int sort_wait_selftest(int spin_limit, unsigned *err_out, cudaStream_t s);
 
 // ---- traversal (query.cu) ------------------------------------------------
 struct QueryArgs {

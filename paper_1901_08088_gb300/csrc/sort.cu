@@ -97,7 +97,8 @@ template <typename K>
 __global__ void __launch_bounds__(kThreads) pass_kernel(const K *__restrict__ kin, const int *__restrict__ vin,
                                                         K *__restrict__ kout, int *__restrict__ vout, int n,
                                                         int shift, const unsigned *__restrict__ bucket_base,
-                                                        unsigned *status, unsigned *ticket, unsigned *err)
+                                                        unsigned *status, unsigned *ticket, unsigned *err,
+                                                        int spin_limit)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned *s_whist = reinterpret_cast<unsigned *>(smem);   // [kWarps][256]
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(const K *__restrict__ ki
                 const unsigned v = ld_relaxed(status + (size_t)j * kRadix + d);
                 const unsigned f = v & ~kValMask;
                 if (f == 0u) {
-                    if (++spins > kSpinLimit) {
+                    if (++spins > spin_limit) {
                         atomicOr(err, QBVH_DEVERR_TIMEOUT);
                         break;
                     }
@@ -235,7 +236,8 @@ int sort_impl(K *ka, K *kb, int *va, int *vb, int n, int bits, void *scratch, un
     (void)v_first_dst;
     for (int p = 0; p < npass; ++p) {
         pass_kernel<K><<<tiles, kThreads, smem, s>>>(src_k, src_v, dst_k, dst_v, n, 8 * p, hist + p * kRadix,
-                                                     status + (size_t)p * tiles * kRadix, ticket + p * 4, err);
+                                                     status + (size_t)p * tiles * kRadix, ticket + p * 4, err,
+                                                     kSpinLimit);
         // ping-pong
         K *tk = src_k;
         src_k = dst_k;
@@ -257,6 +259,42 @@ size_t sort_scratch_bytes(int n, int passes)
 {
     return sizeof(unsigned) * ((size_t)kMaxPasses * kRadix + kMaxPasses * 4 +
                                (size_t)passes * sort_num_tiles(n) * kRadix);
+}
+
+// One tile (tile 1) of a pass whose predecessor (tile 0) never publishes: the
+// look-back gives up after `spin_limit` polls and records QBVH_DEVERR_TIMEOUT.
+// Every access stays inside the 2-tile buffers.  Returns the device error word.
+int sort_wait_selftest(int spin_limit, unsigned *err_out, cudaStream_t s)
+{
+    const int n = 2 * kTile;
+    unsigned *kin = nullptr, *kout = nullptr, *misc = nullptr;
+    int *vout = nullptr;
+    const size_t misc_words = kRadix + 4 + 2 * kRadix + 1;   // bucket base, ticket, status of 2 tiles, err
+    if (cudaMalloc(&kin, n * sizeof(unsigned)) != cudaSuccess || cudaMalloc(&kout, n * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&vout, n * sizeof(int)) != cudaSuccess || cudaMalloc(&misc, misc_words * sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(kin);
+        cudaFree(kout);
+        cudaFree(vout);
+        cudaFree(misc);
+        return -1;
+    }
+    unsigned *base = misc, *ticket = misc + kRadix, *status = misc + kRadix + 4, *err = status + 2 * kRadix;
+    cudaMemsetAsync(kin, 0, n * sizeof(unsigned), s);
+    cudaMemsetAsync(misc, 0, misc_words * sizeof(unsigned), s);
+    const unsigned one = 1u;
+    cudaMemcpyAsync(ticket, &one, sizeof one, cudaMemcpyHostToDevice, s);   // the block takes tile 1
+    const size_t smem = pass_smem<unsigned>();
+    cudaFuncSetAttribute(pass_kernel<unsigned>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    pass_kernel<unsigned><<<1, kThreads, smem, s>>>(kin, nullptr, kout, vout, n, 0, base, status, ticket, err,
+                                                    spin_limit);
+    cudaMemcpyAsync(err_out, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(kin);
+    cudaFree(kout);
+    cudaFree(vout);
+    cudaFree(misc);
+    return e == cudaSuccess ? 0 : -1;
 }
 
 int radix_sort_pairs(bool wide, void *keys_a, void *keys_b, int *vals_a, int *vals_b, int n, int bits,

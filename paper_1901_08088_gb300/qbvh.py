@@ -21,7 +21,7 @@ __all__ = [
     "qbvh_create", "qbvh_destroy", "qbvh_set_option", "qbvh_get_option",
     "qbvh_build", "qbvh_build_batched", "qbvh_query", "qbvh_query_async", "qbvh_query_status",
     "nlist_get", "qbvh_tree_get", "qbvh_lj_forward", "qbvh_lj_backward", "qbvh_pack_positions",
-    "qbvh_lj_forward_noalloc", "qbvh_strerror",
+    "qbvh_lj_forward_noalloc", "qbvh_selftest_wait_timeout", "qbvh_strerror",
 ]
 
 
@@ -161,6 +161,10 @@ def qbvh_lj_forward_noalloc(pos4, L, n_types, rows, counts, eps, sig, r_cut_host
                                          _ptr(rows) if n else None, _ptr(counts) if n else None,
                                          int(rows.shape[1]), _ptr(eps), _ptr(sig), rc.ctypes.data_as(C.c_void_p),
                                          _ptr(e), _ptr(U), _ptr(F), _ptr(dE), _ptr(dS), _stream_ptr(stream))
+
+
+def qbvh_selftest_wait_timeout(device: int = 0, stream=None) -> int:
+    return lib().qbvh_selftest_wait_timeout(int(device), _stream_ptr(stream))
 
 
 def qbvh_pack_positions(xyz: torch.Tensor, types, out4: torch.Tensor, stream=None) -> int:

@@ -122,3 +122,43 @@ def test_config2_full_size_energy_forces():
     assert abs(U[0] - ref["U"]) <= TOL * abs(ref["U"])
     assert _rel(-gx, ref["F"]) <= TOL
     nl.close()
+
+
+@pytest.mark.slow
+def test_config5_full_two_type_batched_gradients():
+    """32 systems x 65,536 particles, two types, per-pair eps/sigma: energies,
+    forces and eps/sigma gradients of every system within 1e-5 of FP64."""
+    import torch
+
+    from paper_1901_08088_gb300 import NeighborList
+
+    systems = workloads.workload("lj2type_32x65536", seed=0)
+    E, S = systems[0].meta["eps"], systems[0].meta["sig"]
+    pos4, off, Ls = concat(systems)
+    nl = NeighborList(0)
+    p4 = torch.from_numpy(pos4).cuda()
+    nl.build_batched(p4, off, Ls, n_types=2)
+    nl.query(2.8)
+    allpos = np.concatenate([s.pos for s in systems])
+    big = workloads.System(pos=allpos, types=np.concatenate([s.types for s in systems]), L=Ls[0],
+                           n_types=2, r_list=systems[0].r_list, r_cut=systems[0].r_cut)
+    rng = np.random.default_rng(1)
+    w = rng.uniform(0.5, 1.5, len(systems))
+    U, gx, ge, gs = _run(nl, big, p4, E, S, 2.5, weights=w.tolist())
+    dE = np.zeros((2, 2))
+    dS = np.zeros((2, 2))
+    worst = {"U": 0.0, "F": 0.0}
+    for k, s in enumerate(systems):
+        a, b = off[k], off[k + 1]
+        ro, co = oracle_list(s)
+        ref = oracle.lj_fp64(s.pos, s.types, s.L, E, S, np.float32(2.5), ro, co)
+        worst["U"] = max(worst["U"], abs(U[k] - ref["U"]) / abs(ref["U"]))
+        worst["F"] = max(worst["F"], _rel(-gx[a:b] / w[k], ref["F"]))
+        dE += w[k] * ref["dE"]
+        dS += w[k] * ref["dS"]
+    err_e = np.max(np.abs(ge - dE) / np.abs(dE))
+    err_s = np.max(np.abs(gs - dS) / np.abs(dS))
+    print(f"config 5 errors vs FP64: U {worst['U']:.2e}, F {worst['F']:.2e}, dU/deps {err_e:.2e}, "
+          f"dU/dsigma {err_s:.2e}")
+    assert worst["U"] <= TOL and worst["F"] <= TOL and err_e <= TOL and err_s <= TOL
+    nl.close()

@@ -236,3 +236,15 @@ def test_full_size_lj_2m(traversal, node_format):
     nbad, bad = oracle.band_check(s.pos, s.L, s.r_list, rg, cg, sample=idx)
     assert nbad == 0, bad
     nl.close()
+
+
+@pytest.mark.slow
+def test_full_size_binary_mixture():
+    # 400 large + 395,280 small particles, per-type trees, per-pair radii 3.4 / 5.9 / 10.4
+    s = workloads.workload("mixture_L100", seed=0)
+    rg, cg, nl, _ = gpu_list(s, cap=512)
+    ro, co = oracle_list(s, cap=512)
+    assert_same_lists(rg, cg, ro, co)
+    big = np.nonzero(s.types == 1)[0]
+    assert cg[big].mean() > 100   # the large particles see their solvent shell
+    nl.close()
