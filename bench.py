@@ -193,6 +193,8 @@ def run_ours(args):
         explicit[_lib.QBVH_OPT_NODE_FORMAT] = args.node_format
     if args.lj_lanes:
         explicit[_lib.QBVH_OPT_LJ_LANES] = args.lj_lanes
+    if args.lj_zorder >= 0:
+        explicit[_lib.QBVH_OPT_LJ_ZORDER] = args.lj_zorder
     tuned, tune_evals = dict(explicit), 0
     if not args.no_autotune:
         def tune_step(opts):
@@ -485,6 +487,7 @@ def main():
     ap.add_argument("--bundle", type=int, default=0, help="subtree-collapse size K (0: library default)")
     ap.add_argument("--block", type=int, default=0, help="traversal threads per block (0: library default)")
     ap.add_argument("--lj-lanes", type=int, default=0, help="lanes per particle in the LJ pass (0: default)")
+    ap.add_argument("--lj-zorder", type=int, default=-1, help="LJ pass in Z-order (1) or original order (0)")
     ap.add_argument("--node-format", type=int, default=-1,
                     help="0: 10-bit quantized nodes, 1: FP32 nodes (-1: library default)")
     ap.add_argument("--traversal", type=int, default=-1,

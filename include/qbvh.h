@@ -101,8 +101,13 @@ int qbvh_destroy(qbvh_handle h);
  * the same list.  Takes effect at the next build. */
 #define QBVH_OPT_NODE_FORMAT 5
 /* Lanes that share one particle's row in qbvh_lj_forward: 1, 2, 4, 8, 16 or
- * 32 (default 8).  More lanes read a row in longer contiguous chunks. */
+ * 32 (default 2).  More lanes read a row in longer contiguous chunks. */
 #define QBVH_OPT_LJ_LANES 6
+/* 1 (default): qbvh_lj_forward visits particles in the Z-order of the last
+ * build (neighbouring particles share cached positions); 0: original order.
+ * Results are the same up to FP32 rounding of the per-block FP64 sums'
+ * inputs (each particle's own sums are unchanged). */
+#define QBVH_OPT_LJ_ZORDER 7
 
 int qbvh_set_option(qbvh_handle h, int option, int value);
 int qbvh_get_option(qbvh_handle h, int option, int *value);

@@ -31,6 +31,7 @@ QBVH_OPT_CANDIDATES = 3
 QBVH_OPT_TRAVERSAL = 4
 QBVH_OPT_NODE_FORMAT = 5
 QBVH_OPT_LJ_LANES = 6
+QBVH_OPT_LJ_ZORDER = 7
 
 _lock = threading.Lock()
 _lib = None

@@ -33,7 +33,7 @@ DEFAULTS = {
     _lib.QBVH_OPT_NODE_FORMAT: 0,
     _lib.QBVH_OPT_TRAVERSAL: 1,
     _lib.QBVH_OPT_QUERY_BLOCK: 128,
-    _lib.QBVH_OPT_LJ_LANES: 8,
+    _lib.QBVH_OPT_LJ_LANES: 2,
 }
 
 _NAMES = {

@@ -50,7 +50,8 @@ struct qbvh_ctx {
     int candidates = 0;
     int traversal = 1;
     int node_fmt = 0;      // 0: 10-bit quantized nodes (Fig. 3b), 1: FP32 nodes (Fig. 3a)
-    int lj_tpp = 8;        // lanes per particle in the LJ pass
+    int lj_tpp = 2;        // lanes per particle in the LJ pass
+    int lj_zorder = 1;     // LJ pass walks particles in the tree's Z-order
     int built_fmt = 0;     // node format of the last build
     // last build
     bool built = false;
@@ -446,6 +447,10 @@ int qbvh_set_option(qbvh_handle h, int option, int value)
         if (value < 1 || value > 32 || (value & (value - 1))) return QBVH_ERR_INVALID_ARG;
         h->lj_tpp = value;
         return QBVH_OK;
+    case QBVH_OPT_LJ_ZORDER:
+        if (value != 0 && value != 1) return QBVH_ERR_INVALID_ARG;
+        h->lj_zorder = value;
+        return QBVH_OK;
     default: return QBVH_ERR_INVALID_ARG;
     }
 }
@@ -460,6 +465,7 @@ int qbvh_get_option(qbvh_handle h, int option, int *value)
     case QBVH_OPT_TRAVERSAL: *value = h->traversal; return QBVH_OK;
     case QBVH_OPT_NODE_FORMAT: *value = h->node_fmt; return QBVH_OK;
     case QBVH_OPT_LJ_LANES: *value = h->lj_tpp; return QBVH_OK;
+    case QBVH_OPT_LJ_ZORDER: *value = h->lj_zorder; return QBVH_OK;
     default: return QBVH_ERR_INVALID_ARG;
     }
 }
@@ -586,6 +592,7 @@ int qbvh_lj_forward(qbvh_handle h, const void *pos_dev, const float *eps_dev, co
     rc = ensure(h, h->lj_partials, (size_t)(h->lj_n_blocks > 0 ? h->lj_n_blocks : 1) * np * 8);
     if (rc) return rc;
     a.pos = reinterpret_cast<const float4 *>(pos_dev);
+    a.order = h->lj_zorder ? reinterpret_cast<const int *>(h->vals[h->sorted].p) : nullptr;
     a.rows = reinterpret_cast<const int *>(h->rows.p);
     a.counts = reinterpret_cast<const int *>(h->counts.p);
     a.cap = h->cap;

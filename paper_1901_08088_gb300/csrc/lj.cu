@@ -22,10 +22,6 @@ namespace {
 
 constexpr int kLJBlock = 128;
 constexpr int kLJParticles = 256;   // particles per block, taken in rounds of kLJBlock / TPP
-#ifndef QBVH_LJ_UNROLL
-#define QBVH_LJ_UNROLL 4
-#endif
-constexpr int kLJUnroll = QBVH_LJ_UNROLL;   // row entries per lane in flight
 
 __device__ __forceinline__ float mi_component(float d, float L, float Linv)
 {
@@ -61,8 +57,12 @@ __global__ void __launch_bounds__(kLJBlock) lj_forward_kernel(const __grid_const
 #pragma unroll
     for (int q = 0; q < NP; ++q) v[q] = 0.0;
     for (int base = a.blk_first[blockIdx.x]; base < end; base += kLJBlock / TPP) {
-        const int i = base + tid / TPP;
-        const bool active = i < end;
+        // position in the walk order: Z-order when the tree's order is given, so
+        // that a block's particles are close and their neighbours' positions are
+        // shared in L1; systems occupy the same index range in both orders
+        const int sidx = base + tid / TPP;
+        const bool active = sidx < end;
+        const int i = active ? (a.order ? __ldg(a.order + sidx) : sidx) : 0;
         float e = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
         float gE[T], gS[T];
 #pragma unroll
@@ -74,22 +74,22 @@ __global__ void __launch_bounds__(kLJBlock) lj_forward_kernel(const __grid_const
             ta = ta < 0 ? 0 : (ta >= T ? T - 1 : ta);
             const int c = min(__ldg(a.counts + i), a.cap);
             const int *row = a.rows + (size_t)i * a.cap;
-            // U row entries per lane are loaded before their positions, and all U
-            // positions before any arithmetic, to keep several loads in flight
-            for (int k0 = sub; k0 < c; k0 += TPP * kLJUnroll) {
-                int jj[kLJUnroll];
-                float4 pp[kLJUnroll];
+            // each lane reads 4 consecutive row entries with one 16-byte load
+            // (rows are 16-byte aligned: the capacity is a multiple of 4), then
+            // the 4 positions, then does the arithmetic
+            const int4 *row4 = reinterpret_cast<const int4 *>(row);
+            for (int k0 = 4 * sub; k0 < c; k0 += 4 * TPP) {
+                const int4 v = __ldg(row4 + (k0 >> 2));
+                int jj[4] = {v.x, v.y, v.z, v.w};
+                float4 pp[4];
 #pragma unroll
-                for (int u = 0; u < kLJUnroll; ++u) {
-                    const int k = k0 + u * TPP;
-                    jj[u] = k < c ? __ldg(row + k) : -1;
+                for (int u = 0; u < 4; ++u) {
+                    if (k0 + u >= c) jj[u] = -1;   // past the row end
+                    if ((unsigned)jj[u] < (unsigned)a.n) pp[u] = __ldg(a.pos + jj[u]);
                 }
 #pragma unroll
-                for (int u = 0; u < kLJUnroll; ++u)
-                    if ((unsigned)jj[u] < (unsigned)a.n) pp[u] = __ldg(a.pos + jj[u]);
-#pragma unroll
-                for (int u = 0; u < kLJUnroll; ++u) {
-                    if ((unsigned)jj[u] >= (unsigned)a.n) continue;   // past the row end
+                for (int u = 0; u < 4; ++u) {
+                    if ((unsigned)jj[u] >= (unsigned)a.n) continue;
                     const float4 pj = pp[u];
                     int tb = T > 1 ? __float_as_int(pj.w) : 0;
                     tb = tb < 0 ? 0 : (tb >= T ? T - 1 : tb);

@@ -147,6 +147,7 @@ void launch_query(const QueryArgs &a, cudaStream_t s);
 // ---- Lennard-Jones (lj.cu) -----------------------------------------------
 struct LJArgs {
     const float4 *pos;
+    const int *order;      // sorted position -> original index (walk order), or nullptr
     const int *rows;
     const int *counts;
     int cap;

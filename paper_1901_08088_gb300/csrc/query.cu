@@ -266,10 +266,12 @@ __device__ __forceinline__ Frame frame_of(const SegInfo &g)
     return f;
 }
 
-// node id outside the tree [start, last] -> broken structure
+// node id outside the tree [start, last] -> broken structure (one unsigned
+// compare on the node's or the leaf's index)
 __device__ __forceinline__ bool bad_node(int node, const SegInfo &g, int last)
 {
-    return node >= 0 ? (node < g.start || node > last) : (~node < g.start || ~node > last);
+    const int idx = node ^ (node >> 31);   // node for internal ids, ~node for leaves
+    return (unsigned)(idx - g.start) > (unsigned)(last - g.start);
 }
 
 // Largest row count: one atomic per warp, skipped when it cannot raise the maximum.
@@ -369,6 +371,17 @@ __global__ void query_thread_kernel(const __grid_constant__ QueryArgs a)
     warp_max_count(my_count, a.status);
 }
 
+// Registers are capped so that 8 blocks of 256 threads (64 warps) fit on an
+// SM: the walk is latency-bound and more resident warps hide more of it
+// (measured 2.37 -> 2.23 ms at N = 2M despite a few spilled bytes).
+#ifndef QBVH_QUERY_MIN_BLOCKS
+#define QBVH_QUERY_MIN_BLOCKS 8
+#endif
+// bundle leaves tested two per step (two loads in flight; measured 2.25 ->
+// 2.20 ms at N = 2M) or one per step
+#ifndef QBVH_LEAF_PAIRS
+#define QBVH_LEAF_PAIRS 1
+#endif
 // ---- one warp per 32 consecutive Z-order particles ----------------------
 // The warp-uniform rope walk of one tree under one periodic image.
 template <bool CAND, int FMT, bool SHIFT>
@@ -393,7 +406,18 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                         atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
                         l = nd.left - 1;
                     }
-                    for (int j = nd.left; j <= l; ++j) {
+                    int j = nd.left;
+#if QBVH_LEAF_PAIRS
+                    for (; j < l; j += 2) {   // two leaves per step: two loads in flight
+                        const float4 q0 = __ldg(a.leaves + j);
+                        const float4 q1 = __ldg(a.leaves + j + 1);
+                        if (on) {
+                            test_leaf<CAND, SHIFT>(a, c, out, j, q0, f, rs2);
+                            test_leaf<CAND, SHIFT>(a, c, out, j + 1, q1, f, rs2);
+                        }
+                    }
+#endif
+                    for (; j <= l; ++j) {
                         const float4 q = __ldg(a.leaves + j);
                         if (on) test_leaf<CAND, SHIFT>(a, c, out, j, q, f, rs2);
                     }
@@ -413,12 +437,6 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
     }
 }
 
-// Registers are capped so that 8 blocks of 256 threads (64 warps) fit on an
-// SM: the walk is latency-bound and more resident warps hide more of it
-// (measured 2.37 -> 2.23 ms at N = 2M despite a few spilled bytes).
-#ifndef QBVH_QUERY_MIN_BLOCKS
-#define QBVH_QUERY_MIN_BLOCKS 8
-#endif
 #if QBVH_QUERY_MIN_BLOCKS > 0
 #define QBVH_QUERY_BOUNDS __launch_bounds__(256, QBVH_QUERY_MIN_BLOCKS)
 #else

@@ -32,13 +32,15 @@ def _run(nl, s, pos4, E, S, rc, weights=None):
     return U.detach().cpu().numpy(), xyz.grad.cpu().numpy(), eps.grad.cpu().numpy(), sig.grad.cpu().numpy()
 
 
+@pytest.mark.parametrize("zorder", [0, 1])
 @pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
-def test_single_type_energy_forces(lanes):
+def test_single_type_energy_forces(lanes, zorder):
     from paper_1901_08088_gb300 import _lib
 
     s = workloads.workload("lj_n4096_rho0.6", seed=1)
     rg, cg, nl, pos4 = gpu_list(s)
     nl.set_option(_lib.QBVH_OPT_LJ_LANES, lanes)
+    nl.set_option(_lib.QBVH_OPT_LJ_ZORDER, zorder)
     U, gx, ge, gs = _run(nl, s, pos4, [[1.0]], [[1.0]], 3.0)
     ro, co = oracle_list(s, method="brute")
     ref = oracle.lj_fp64(s.pos, s.types, s.L, [[1.0]], [[1.0]], np.float32(3.0), ro, co)
