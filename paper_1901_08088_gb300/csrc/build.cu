@@ -349,6 +349,14 @@ __device__ __forceinline__ int rope_after(const int2 *range, int last, int hi)
 
 __device__ __forceinline__ float clear_sign(float x) { return __int_as_float(__float_as_int(x) & 0x7FFFFFFF); }
 
+// atomic increment with acquire-release semantics at device scope; returns the old value
+__device__ __forceinline__ int arrive_acq_rel(int *p)
+{
+    int old;
+    asm volatile("atom.add.acq_rel.gpu.s32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+    return old;
+}
+
 template <bool WIDE, bool F32>
 __global__ void __launch_bounds__(kBlock) fit_kernel(const BuildArgs a)
 {
@@ -382,8 +390,9 @@ __global__ void __launch_bounds__(kBlock) fit_kernel(const BuildArgs a)
             atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
             return;
         }
-        __threadfence();   // publish this child's bounds before arriving
-        if (atomicAdd(a.visit + node, 1) == 0) return;   // sibling not done yet
+        // arrive: release publishes this child's bounds, acquire makes the
+        // sibling's bounds visible to the thread that continues upward
+        if (arrive_acq_rel(a.visit + node) == 0) return;   // sibling not done yet
         const int2 c = a.child[node];
         if (c.x >= a.n || ~c.x >= a.n || c.y >= a.n || ~c.y >= a.n) {
             atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);

@@ -22,7 +22,13 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 16;
+// keys per thread: 8 keeps 2048-key tiles, 27 KB of shared memory per block
+// and twice the blocks of 16 items (the pass is latency-bound: more resident
+// tiles hide more of the ranking and look-back latency)
+#ifndef QBVH_SORT_ITEMS
+#define QBVH_SORT_ITEMS 8
+#endif
+constexpr int kItems = QBVH_SORT_ITEMS;
 constexpr int kTile = kThreads * kItems;
 constexpr int kRadix = 256;
 constexpr unsigned kFlagAgg = 1u << 30;
