@@ -191,6 +191,8 @@ def run_ours(args):
         explicit[_lib.QBVH_OPT_TRAVERSAL] = args.traversal
     if args.node_format >= 0:
         explicit[_lib.QBVH_OPT_NODE_FORMAT] = args.node_format
+    if args.warp_particles:
+        explicit[_lib.QBVH_OPT_WARP_PARTICLES] = args.warp_particles
     if args.lj_lanes:
         explicit[_lib.QBVH_OPT_LJ_LANES] = args.lj_lanes
     if args.lj_zorder >= 0:
@@ -327,6 +329,8 @@ def run_ours(args):
             out["config"]["workload"] = f"profiling case: LJ fluid N={n} rho=0.8 (not a bench result)"
         if not args.no_batched and world == 1:
             out["batched"] = run_batched(args, local)
+        if not args.no_grid_compare and world == 1 and not args.n:
+            out["grid_comparison"] = run_grid_comparison(args, local)
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(s, samples=1)
         elif world == 1:
@@ -400,6 +404,46 @@ def run_batched(args, local):
         "graph_ms": graph_ms, "loop_ms": loop_ms, "ratio": loop_ms / graph_ms,
         "options": autotune.option_names(best),
     }
+
+
+def run_grid_comparison(args, local):
+    """The paper's comparison (Sec. 4): quantized BVH vs an equivalent sort-based
+    uniform grid, build + query of the exact list, on synthetic stand-ins of its
+    LJ state points (N = 128,000, r_c = 3.0, rho 0.2 and 0.8; N scan at rho 0.6)
+    and on the bench workload.  Each method gets a small autotune."""
+    import torch
+
+    import workloads
+    from paper_1901_08088_gb300 import NeighborList, _lib, autotune
+
+    cases = [("paper LJ rho 0.2", 128_000, 0.2, 3.0, 0.0), ("paper LJ rho 0.8", 128_000, 0.8, 3.0, 0.0)]
+    cases += [(f"N scan rho 0.6", n, 0.6, 3.0, 0.0) for n in (1_000, 4_096, 16_384, 65_536)]
+    cases += [("bench workload", 2_097_152, 0.8, 3.0, 0.3)]
+    out = []
+    for label, n, rho, rc, skin in cases:
+        s = workloads.jittered_lattice(n, rho, 0.25 if n == 2_097_152 else 0.3, seed=0, r_cut=rc, skin=skin)
+        pos4 = torch.from_numpy(workloads.pack_float4(s.pos, s.types)).cuda()
+        res = {"workload": label, "n": n, "rho": rho, "r_list": float(s.r_list[0, 0])}
+        for method, space in ((0, {_lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8], _lib.QBVH_OPT_BUNDLE: [8, 16],
+                                    _lib.QBVH_OPT_NODE_FORMAT: [1, 0]}),
+                              (1, {_lib.QBVH_OPT_GRID_LANES: [2, 4, 8, 16]})):
+            nl = NeighborList(local)
+            nl.set_option(_lib.QBVH_OPT_METHOD, method)
+
+            def step(opts, nl=nl, pos4=pos4, s=s):
+                for k, v in opts.items():
+                    nl.set_option(k, v)
+                nl.build(pos4, s.L)
+                nl.query(s.r_list, cap=CAP)
+
+            start = {k: v[0] for k, v in space.items()}
+            best, ms, _ = autotune.tune(step, space=space, start=start, reps=5, warmup=2, sweeps=1)
+            res["bvh_ms" if method == 0 else "grid_ms"] = ms
+            res["bvh_options" if method == 0 else "grid_options"] = autotune.option_names(best)
+            nl.close()
+        res["bvh_speedup_over_grid"] = res["grid_ms"] / res["bvh_ms"]
+        out.append(res)
+    return out
 
 
 def cpu_baseline(s, samples=1):
@@ -481,6 +525,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-system graph-vs-loop measurement")
+    ap.add_argument("--no-grid-compare", action="store_true", help="skip the BVH-vs-grid comparison")
     ap.add_argument("--n", type=int, default=0,
                     help="profiling aid: run the same fluid with N particles instead of 2,097,152 "
                          "(the line it prints is not a bench result)")
@@ -488,6 +533,7 @@ def main():
     ap.add_argument("--block", type=int, default=0, help="traversal threads per block (0: library default)")
     ap.add_argument("--lj-lanes", type=int, default=0, help="lanes per particle in the LJ pass (0: default)")
     ap.add_argument("--lj-zorder", type=int, default=-1, help="LJ pass in Z-order (1) or original order (0)")
+    ap.add_argument("--warp-particles", type=int, default=0, help="particles per warp of the walk (0: default)")
     ap.add_argument("--node-format", type=int, default=-1,
                     help="0: 10-bit quantized nodes, 1: FP32 nodes (-1: library default)")
     ap.add_argument("--traversal", type=int, default=-1,

@@ -108,6 +108,23 @@ int qbvh_destroy(qbvh_handle h);
  * Results are the same up to FP32 rounding of the per-block FP64 sums'
  * inputs (each particle's own sums are unchanged). */
 #define QBVH_OPT_LJ_ZORDER 7
+/* Search method: 0 (default) = the quantized BVH; 1 = the paper's comparison
+ * method, a sort-based uniform grid (cell list) with cells as wide as the
+ * largest list radius and a 27-cell stencil walked by QBVH_OPT_GRID_LANES
+ * lanes per particle (Sec. 3).  Same exact list.  With the grid, qbvh_build
+ * only records the input (one system, positions kept alive by the caller
+ * until the query has run) and the grid is built inside qbvh_query, because
+ * the cell width is the list radius; qbvh_tree_get is not available.
+ * Takes effect at the next build. */
+#define QBVH_OPT_METHOD 8
+/* Lanes per particle of the grid traversal: 1, 2, 4, 8, 16 or 32 (default 8). */
+#define QBVH_OPT_GRID_LANES 9
+/* Particles per warp of the warp-uniform walk: 32 (default), 16 or 8; with
+ * fewer particles each particle gets 32/value lanes, which split a bundle's
+ * leaves and pack their accepted neighbours with a ballot.  Fewer particles
+ * per warp means more warps (small systems fill the GPU) and a smaller union
+ * of search spheres per walk. */
+#define QBVH_OPT_WARP_PARTICLES 10
 
 int qbvh_set_option(qbvh_handle h, int option, int value);
 int qbvh_get_option(qbvh_handle h, int option, int *value);

@@ -32,6 +32,9 @@ QBVH_OPT_TRAVERSAL = 4
 QBVH_OPT_NODE_FORMAT = 5
 QBVH_OPT_LJ_LANES = 6
 QBVH_OPT_LJ_ZORDER = 7
+QBVH_OPT_METHOD = 8
+QBVH_OPT_GRID_LANES = 9
+QBVH_OPT_WARP_PARTICLES = 10
 
 _lock = threading.Lock()
 _lib = None

@@ -24,6 +24,7 @@ OPTION_SPACE = {
     _lib.QBVH_OPT_BUNDLE: [4, 8, 16, 32],
     _lib.QBVH_OPT_NODE_FORMAT: [0, 1],
     _lib.QBVH_OPT_TRAVERSAL: [1, 0],
+    _lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8],
     _lib.QBVH_OPT_QUERY_BLOCK: [64, 128, 256],
     _lib.QBVH_OPT_LJ_LANES: [1, 2, 4, 8],
 }
@@ -32,6 +33,7 @@ DEFAULTS = {
     _lib.QBVH_OPT_BUNDLE: 16,
     _lib.QBVH_OPT_NODE_FORMAT: 0,
     _lib.QBVH_OPT_TRAVERSAL: 1,
+    _lib.QBVH_OPT_WARP_PARTICLES: 32,
     _lib.QBVH_OPT_QUERY_BLOCK: 128,
     _lib.QBVH_OPT_LJ_LANES: 2,
 }
@@ -42,6 +44,10 @@ _NAMES = {
     _lib.QBVH_OPT_TRAVERSAL: "traversal",
     _lib.QBVH_OPT_QUERY_BLOCK: "query_block",
     _lib.QBVH_OPT_LJ_LANES: "lj_lanes",
+    _lib.QBVH_OPT_WARP_PARTICLES: "warp_particles",
+    _lib.QBVH_OPT_GRID_LANES: "grid_lanes",
+    _lib.QBVH_OPT_METHOD: "method",
+    _lib.QBVH_OPT_LJ_ZORDER: "lj_zorder",
 }
 
 

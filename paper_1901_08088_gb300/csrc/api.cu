@@ -49,9 +49,14 @@ struct qbvh_ctx {
     int query_block = 128;
     int candidates = 0;
     int traversal = 1;
+    int warp_particles = 32;
     int node_fmt = 0;      // 0: 10-bit quantized nodes (Fig. 3b), 1: FP32 nodes (Fig. 3a)
     int lj_tpp = 2;        // lanes per particle in the LJ pass
     int lj_zorder = 1;     // LJ pass walks particles in the tree's Z-order
+    int method = 0;        // 0: quantized BVH, 1: uniform grid comparator
+    int grid_tpp = 8;      // lanes per particle of the grid traversal
+    int built_method = 0;
+    const void *grid_pos = nullptr;   // positions recorded by a grid-method build
     int built_fmt = 0;     // node format of the last build
     // last build
     bool built = false;
@@ -71,6 +76,7 @@ struct qbvh_ctx {
     DevBuf keys[2], vals[2], sort_scratch, nodes, nodes32, leaves, leaf_q, range, child, par_int, par_leaf, visit;
     DevBuf seg, acc, seg_start, frames, sys, sys_off, status;
     DevBuf rows, counts;
+    DevBuf cell_start, stype;
     DevBuf lj_partials, lj_blk_sys, lj_blk_first, lj_sys_blk;
     std::vector<int> lj_layout_off;   // offsets the LJ block tables were built for
     int lj_n_blocks = 0;
@@ -202,6 +208,20 @@ int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *of
         h->L_min = fminf(h->L_min, L[k]);
         h->L_max = fmaxf(h->L_max, L[k]);
     }
+    h->built_method = h->method;
+    if (h->method == 1) {
+        // grid comparator: the cell width is the list radius, known at the query;
+        // the build records the input and the system description only
+        if (n_sys != 1) return QBVH_ERR_INVALID_ARG;
+        int rc0 = ensure(h, h->status, sizeof(DevStatus));
+        rc0 = rc0 ? rc0 : upload_if_changed(h, h->sys, h->up_sys, h->sysinfo, s);
+        rc0 = rc0 ? rc0 : upload_if_changed(h, h->sys_off, h->up_off, h->off, s);
+        if (rc0) return rc0;
+        if (cudaMemsetAsync(h->status.p, 0, sizeof(DevStatus), s) != cudaSuccess) return QBVH_ERR_CUDA;
+        h->grid_pos = pos_dev;
+        h->built = true;
+        return QBVH_OK;
+    }
     const int bits = h->wide ? 30 + ceil_log2(h->n_seg) : (n_types > 1 ? 32 : 30);
     const int passes = (bits + 7) / 8;
     const size_t kb = h->wide ? 8 : 4;
@@ -284,6 +304,66 @@ int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *of
     return QBVH_OK;
 }
 
+// Grid comparator: bin into cells at least the largest list radius wide (with
+// a 2^-14 relative margin that absorbs the FP32 binning round-off, so two
+// particles closer than the radius always sit in adjacent cells), sort by
+// cell, find every cell's first particle, gather, walk the 27-cell stencil.
+int grid_enqueue(qbvh_ctx *h, const float *r_list, const float *rl2, int cap, cudaStream_t s)
+{
+    const int T = h->n_types;
+    float rmax = 0.f;
+    for (int p = 0; p < T * T; ++p) rmax = fmaxf(rmax, r_list[p]);
+    const float L = h->L[0];
+    const int n = h->n;
+    int nc = rmax > 0.f ? (int)floor((double)L / ((double)rmax * (1.0 + ldexp(1.0, -14)))) : 1023;
+    // no more than about 2 cells per particle (wider cells stay correct)
+    const int nc_cap = (int)ceil(cbrt(2.0 * (n > 27 ? n : 27)));
+    if (nc > nc_cap) nc = nc_cap;
+    if (nc > 1023) nc = 1023;
+    if (nc < 3) return QBVH_ERR_CUTOFF_TOO_LARGE;
+    const long long ncell = (long long)nc * nc * nc;
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    int rc = QBVH_OK;
+    rc = rc ? rc : ensure(h, h->keys[0], nn * 4);
+    rc = rc ? rc : ensure(h, h->keys[1], nn * 4);
+    rc = rc ? rc : ensure(h, h->vals[0], nn * 4);
+    rc = rc ? rc : ensure(h, h->vals[1], nn * 4);
+    const int bits = ceil_log2((int)ncell + 1);
+    rc = rc ? rc : ensure(h, h->sort_scratch, sort_scratch_bytes(n, (bits + 7) / 8));
+    rc = rc ? rc : ensure(h, h->cell_start, (size_t)(ncell + 1) * 4);
+    rc = rc ? rc : ensure(h, h->leaves, nn * sizeof(float4));
+    if (T > 1) rc = rc ? rc : ensure(h, h->stype, nn * 4);
+    if (rc) return rc;
+    GridArgs a;
+    memset(&a, 0, sizeof a);
+    a.pos = reinterpret_cast<const float4 *>(h->grid_pos);
+    a.n = n;
+    a.n_types = T;
+    a.L = L;
+    a.Linv = 1.0f / L;
+    a.nc = nc;
+    a.inv_w = (float)nc / L;
+    a.keys = reinterpret_cast<unsigned *>(h->keys[0].p);
+    a.cell_start = reinterpret_cast<int *>(h->cell_start.p);
+    a.spos = reinterpret_cast<float4 *>(h->leaves.p);
+    a.stype = T > 1 ? reinterpret_cast<int *>(h->stype.p) : nullptr;
+    a.rows = reinterpret_cast<int *>(h->rows.p);
+    a.counts = reinterpret_cast<int *>(h->counts.p);
+    a.cap = cap;
+    a.tpp = h->grid_tpp;
+    for (int p = 0; p < T * T; ++p) a.rl2[p] = r_list[p] > 0.f ? rl2[p] : -1.f;
+    a.status = reinterpret_cast<DevStatus *>(h->status.p);
+    launch_grid_keys(a, s);
+    h->sorted = radix_sort_pairs(false, h->keys[0].p, h->keys[1].p, reinterpret_cast<int *>(h->vals[0].p),
+                                 reinterpret_cast<int *>(h->vals[1].p), n, bits, h->sort_scratch.p, &a.status->err,
+                                 s);
+    a.keys_sorted = reinterpret_cast<const unsigned *>(h->keys[h->sorted].p);
+    a.order = reinterpret_cast<const int *>(h->vals[h->sorted].p);
+    launch_grid_cells(a, s);
+    launch_grid_query(a, s);
+    return cuda_status();
+}
+
 int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s)
 {
     if (!h) return QBVH_ERR_INVALID_ARG;
@@ -316,6 +396,18 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
     if (rc) return rc;
     DevStatus *st = reinterpret_cast<DevStatus *>(h->status.p);
     if (cudaMemsetAsync(&st->max_count, 0, sizeof(int), s) != cudaSuccess) return QBVH_ERR_CUDA;
+    if (h->built_method == 1) {
+        rc = grid_enqueue(h, q.r_list, q.rl2, cap, s);
+        if (rc) return rc;
+        if (cudaMemcpyAsync(h->h_status, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return QBVH_ERR_CUDA;
+        rc = cuda_status();
+        if (rc) return rc;
+        h->cap = cap;
+        memcpy(h->r_list, q.r_list, sizeof q.r_list);
+        h->have_list = true;
+        return QBVH_OK;
+    }
     q.nodes = reinterpret_cast<const int4 *>(h->nodes.p);
     q.nodes32 = reinterpret_cast<const float4 *>(h->nodes32.p);
     q.node_fmt = h->built_fmt;
@@ -333,6 +425,7 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
     q.status = st;
     q.candidates = h->candidates;
     q.traversal = h->traversal;
+    q.warp_particles = h->warp_particles;
     q.block = h->query_block;
     launch_query(q, s);
     if (cudaMemcpyAsync(h->h_status, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -410,7 +503,7 @@ int qbvh_destroy(qbvh_handle h)
         DevBuf *all[] = {&h->keys[0], &h->keys[1], &h->vals[0], &h->vals[1], &h->sort_scratch, &h->nodes, &h->nodes32,
                          &h->leaves, &h->leaf_q, &h->range, &h->child, &h->par_int, &h->par_leaf, &h->visit,
                          &h->seg, &h->acc, &h->seg_start, &h->frames, &h->sys, &h->sys_off, &h->status,
-                         &h->rows, &h->counts, &h->lj_partials, &h->lj_blk_sys, &h->lj_blk_first,
+                         &h->rows, &h->counts, &h->cell_start, &h->stype, &h->lj_partials, &h->lj_blk_sys, &h->lj_blk_first,
                          &h->lj_sys_blk};
         for (DevBuf *b : all) release(*b);
         if (h->h_status) cudaFreeHost(h->h_status);
@@ -451,6 +544,18 @@ int qbvh_set_option(qbvh_handle h, int option, int value)
         if (value != 0 && value != 1) return QBVH_ERR_INVALID_ARG;
         h->lj_zorder = value;
         return QBVH_OK;
+    case QBVH_OPT_WARP_PARTICLES:
+        if (value != 32 && value != 16 && value != 8) return QBVH_ERR_INVALID_ARG;
+        h->warp_particles = value;
+        return QBVH_OK;
+    case QBVH_OPT_METHOD:
+        if (value != 0 && value != 1) return QBVH_ERR_INVALID_ARG;
+        h->method = value;
+        return QBVH_OK;
+    case QBVH_OPT_GRID_LANES:
+        if (value < 1 || value > 32 || (value & (value - 1))) return QBVH_ERR_INVALID_ARG;
+        h->grid_tpp = value;
+        return QBVH_OK;
     default: return QBVH_ERR_INVALID_ARG;
     }
 }
@@ -466,6 +571,9 @@ int qbvh_get_option(qbvh_handle h, int option, int *value)
     case QBVH_OPT_NODE_FORMAT: *value = h->node_fmt; return QBVH_OK;
     case QBVH_OPT_LJ_LANES: *value = h->lj_tpp; return QBVH_OK;
     case QBVH_OPT_LJ_ZORDER: *value = h->lj_zorder; return QBVH_OK;
+    case QBVH_OPT_WARP_PARTICLES: *value = h->warp_particles; return QBVH_OK;
+    case QBVH_OPT_METHOD: *value = h->method; return QBVH_OK;
+    case QBVH_OPT_GRID_LANES: *value = h->grid_tpp; return QBVH_OK;
     default: return QBVH_ERR_INVALID_ARG;
     }
 }
@@ -532,7 +640,7 @@ int qbvh_tree_get(qbvh_handle h, const void **nodes, const void **leaves, const 
                   const float **frames, int *n_seg)
 {
     if (!h) return QBVH_ERR_INVALID_ARG;
-    if (!h->built) return QBVH_ERR_NOT_BUILT;
+    if (!h->built || h->built_method != 0) return QBVH_ERR_NOT_BUILT;
     if (nodes) *nodes = h->nodes.p;
     if (leaves) *leaves = h->leaves.p;
     if (order) *order = reinterpret_cast<const int *>(h->vals[h->sorted].p);

@@ -134,7 +134,8 @@ struct QueryArgs {
     int *counts;
     DevStatus *status;
     int candidates;        // 1: Alg. 1 candidates, no exact leaf test
-    int traversal;         // 0: one thread per particle, 1: one warp per 32 particles
+    int traversal;         // 0: one thread per particle, 1: warp-uniform walk
+    int warp_particles;    // particles per warp of the warp walk: 32, 16 or 8
     int block;
     float r_list[64];      // [a][b] list radius
     float rl2[64];         // fl(r * r)
@@ -143,6 +144,32 @@ struct QueryArgs {
 };
 
 void launch_query(const QueryArgs &a, cudaStream_t s);
+
+// ---- uniform grid comparator (grid.cu) ----------------------------------
+struct GridArgs {
+    const float4 *pos;     // [n] original order
+    int n;
+    int n_types;
+    float L, Linv;
+    int nc;                // cells per axis
+    float inv_w;           // fl(nc / L)
+    unsigned *keys;        // cell index per particle (sort input)
+    const unsigned *keys_sorted;
+    const int *order;      // sorted position -> original index
+    int *cell_start;       // [nc^3 + 1]
+    float4 *spos;          // [n] positions in cell order, w = original index
+    int *stype;            // [n] types in cell order (n_types > 1) or nullptr
+    int *rows;
+    int *counts;
+    int cap;
+    int tpp;               // lanes per particle
+    float rl2[64];
+    DevStatus *status;
+};
+
+void launch_grid_keys(const GridArgs &a, cudaStream_t s);
+void launch_grid_cells(const GridArgs &a, cudaStream_t s);
+void launch_grid_query(const GridArgs &a, cudaStream_t s);
 
 // ---- Lennard-Jones (lj.cu) -----------------------------------------------
 struct LJArgs {

@@ -207,6 +207,41 @@ __device__ __forceinline__ void test_leaf(const QueryArgs &A, const Query &c, Ro
         exact_leaf<SHIFT>(c, out, j, q);
 }
 
+// The same decisions as exact_leaf / candidate_leaf, returned instead of
+// appended (used when several lanes share one particle's row).
+template <bool CAND, bool SHIFT>
+__device__ __forceinline__ bool leaf_accepts(const QueryArgs &A, const Query &c, int j, const float4 q,
+                                             const Frame &f, float rs2)
+{
+    if (j == c.self) return false;
+    if (CAND) return overlap_q(c.px, c.py, c.pz, __ldg(A.leaf_q + j), f, rs2);
+    float dx = __fsub_rn(q.x, c.xi);
+    float dy = __fsub_rn(q.y, c.yi);
+    float dz = __fsub_rn(q.z, c.zi);
+    if (SHIFT) {
+        dx = __fsub_rn(dx, c.nLx);
+        dy = __fsub_rn(dy, c.nLy);
+        dz = __fsub_rn(dz, c.nLz);
+    }
+    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    return d2 < c.rl2;
+}
+
+// Append for W lanes sharing a row: the lanes of one particle are `same`
+// (a bit pattern over the warp); accepted entries are packed in lane order.
+// Every lane of the warp must call this together.
+__device__ __forceinline__ void push_shared(Row &out, bool acc, int j, unsigned same)
+{
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, acc) & same;
+    if (acc) {
+        unsigned lt;
+        asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+        const int slot = out.count + __popc(m & lt);
+        if (slot < out.cap) __stcs(out.row + slot, j);
+    }
+    out.count += __popc(m);
+}
+
 // 27-bit set of the periodic images whose padded search sphere overlaps the
 // root AABB of a tree (Sec. 2.3): bit 9 (nx+1) + 3 (ny+1) + (nz+1).
 __device__ __forceinline__ unsigned image_mask(float x, float y, float z, float L, const SegInfo &g, float rs2)
@@ -384,9 +419,10 @@ __global__ void query_thread_kernel(const __grid_constant__ QueryArgs a)
 #endif
 // ---- one warp per 32 consecutive Z-order particles ----------------------
 // The warp-uniform rope walk of one tree under one periodic image.
-template <bool CAND, int FMT, bool SHIFT>
+template <bool CAND, int FMT, bool SHIFT, int W>
 __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Row &out, const SegInfo &g,
-                                          const Frame &f, int root, int last, bool on, float rs2)
+                                          const Frame &f, int root, int last, bool on, float rs2, int wsub,
+                                          unsigned same)
 {
     const float lrs2 = on ? rs2 : -1.f;   // a negative squared radius overlaps nothing
     int node = root;
@@ -407,19 +443,34 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                         l = nd.left - 1;
                     }
                     int j = nd.left;
+                    if (W == 1) {
 #if QBVH_LEAF_PAIRS
-                    for (; j < l; j += 2) {   // two leaves per step: two loads in flight
-                        const float4 q0 = __ldg(a.leaves + j);
-                        const float4 q1 = __ldg(a.leaves + j + 1);
-                        if (on) {
-                            test_leaf<CAND, SHIFT>(a, c, out, j, q0, f, rs2);
-                            test_leaf<CAND, SHIFT>(a, c, out, j + 1, q1, f, rs2);
+                        for (; j < l; j += 2) {   // two leaves per step: two loads in flight
+                            const float4 q0 = __ldg(a.leaves + j);
+                            const float4 q1 = __ldg(a.leaves + j + 1);
+                            if (on) {
+                                test_leaf<CAND, SHIFT>(a, c, out, j, q0, f, rs2);
+                                test_leaf<CAND, SHIFT>(a, c, out, j + 1, q1, f, rs2);
+                            }
                         }
-                    }
 #endif
-                    for (; j <= l; ++j) {
-                        const float4 q = __ldg(a.leaves + j);
-                        if (on) test_leaf<CAND, SHIFT>(a, c, out, j, q, f, rs2);
+                        for (; j <= l; ++j) {
+                            const float4 q = __ldg(a.leaves + j);
+                            if (on) test_leaf<CAND, SHIFT>(a, c, out, j, q, f, rs2);
+                        }
+                    } else {
+                        // the W lanes of a particle take every W-th leaf
+                        for (; j <= l; j += W) {
+                            const int jj = j + wsub;
+                            bool acc = false;
+                            int id = 0;
+                            if (jj <= l) {
+                                const float4 q = __ldg(a.leaves + jj);
+                                acc = on && leaf_accepts<CAND, SHIFT>(a, c, jj, q, f, rs2);
+                                id = __float_as_int(q.w) & 0x7FFFFFFF;
+                            }
+                            push_shared(out, acc, id, same);
+                        }
                     }
                     node = nd.rope;
                 } else {
@@ -431,7 +482,12 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
         } else {
             const int j = ~node;
             const float4 q = __ldg(a.leaves + j);
-            if (on) test_leaf<CAND, SHIFT>(a, c, out, j, q, f, rs2);
+            if (W == 1) {
+                if (on) test_leaf<CAND, SHIFT>(a, c, out, j, q, f, rs2);
+            } else {
+                const bool acc = wsub == 0 && on && leaf_accepts<CAND, SHIFT>(a, c, j, q, f, rs2);
+                push_shared(out, acc, __float_as_int(q.w) & 0x7FFFFFFF, same);
+            }
             node = (j == last) ? QBVH_END : ((__float_as_int(q.w) < 0) ? j + 1 : ~(j + 1));
         }
     }
@@ -443,10 +499,18 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
 #define QBVH_QUERY_BOUNDS
 #endif
 
-template <bool WIDE, bool CAND, int FMT>
+// W lanes per particle: a warp serves 32 / W consecutive Z-order particles;
+// lane l works for particle l % (32 / W) and takes every W-th leaf of a bundle
+// starting at l / (32 / W).
+template <bool WIDE, bool CAND, int FMT, int W>
 __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ QueryArgs a)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int G = 32 / W;
+    const int lane = threadIdx.x & 31;
+    const int pidx = lane % G;
+    const int wsub = lane / G;
+    const unsigned same = (W == 1 ? 1u : (W == 2 ? 0x00010001u : (W == 4 ? 0x01010101u : 0x11111111u))) << pidx;
+    const int s = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G + pidx;
     const bool active = s < a.n;
     float4 me = make_float4(0.f, 0.f, 0.f, 0.f);
     int i_orig = 0, seg_i = -1;
@@ -497,41 +561,65 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
                 set_image(c, img, L);
                 const bool on = (mine >> img) & 1u;
                 if (img == 13)
-                    warp_walk<CAND, FMT, false>(a, c, out, g, f, root, last, on, rs2);
+                    warp_walk<CAND, FMT, false, W>(a, c, out, g, f, root, last, on, rs2, wsub, same);
                 else
-                    warp_walk<CAND, FMT, true>(a, c, out, g, f, root, last, on, rs2);
+                    warp_walk<CAND, FMT, true, W>(a, c, out, g, f, root, last, on, rs2, wsub, same);
             }
         }
     }
-    if (active) a.counts[i_orig] = out.count;
+    if (active && wsub == 0) a.counts[i_orig] = out.count;
     warp_max_count(active ? out.count : 0, a.status);
 }
 
 }  // namespace
 
+template <int FMT, int W>
+static void launch_warp(const QueryArgs &a, cudaStream_t s)
+{
+    const int b = a.block;
+    const long long threads = (long long)((a.n + (32 / W) - 1) / (32 / W)) * 32;
+    const int grid = (int)((threads + b - 1) / b);
+    if (a.wide_keys) {
+        if (a.candidates) query_warp_kernel<true, true, FMT, W><<<grid, b, 0, s>>>(a);
+        else query_warp_kernel<true, false, FMT, W><<<grid, b, 0, s>>>(a);
+    } else {
+        if (a.candidates) query_warp_kernel<false, true, FMT, W><<<grid, b, 0, s>>>(a);
+        else query_warp_kernel<false, false, FMT, W><<<grid, b, 0, s>>>(a);
+    }
+}
+
+template <int FMT>
+static void launch_thread(const QueryArgs &a, cudaStream_t s)
+{
+    const int b = a.block;
+    const int grid = (a.n + b - 1) / b;
+    if (a.wide_keys) {
+        if (a.candidates) query_thread_kernel<true, true, FMT><<<grid, b, 0, s>>>(a);
+        else query_thread_kernel<true, false, FMT><<<grid, b, 0, s>>>(a);
+    } else {
+        if (a.candidates) query_thread_kernel<false, true, FMT><<<grid, b, 0, s>>>(a);
+        else query_thread_kernel<false, false, FMT><<<grid, b, 0, s>>>(a);
+    }
+}
+
 void launch_query(const QueryArgs &a, cudaStream_t s)
 {
     if (a.n == 0) return;
-    const int b = a.block;
-    const int grid = (a.n + b - 1) / b;
-#define QBVH_LAUNCH(K, F)                                                            \
-    do {                                                                             \
-        if (a.wide_keys) {                                                           \
-            if (a.candidates) K<true, true, F><<<grid, b, 0, s>>>(a);                \
-            else K<true, false, F><<<grid, b, 0, s>>>(a);                            \
-        } else {                                                                     \
-            if (a.candidates) K<false, true, F><<<grid, b, 0, s>>>(a);               \
-            else K<false, false, F><<<grid, b, 0, s>>>(a);                           \
-        }                                                                            \
-    } while (0)
     if (a.traversal == 0) {
-        if (a.node_fmt == 0) QBVH_LAUNCH(query_thread_kernel, 0);
-        else QBVH_LAUNCH(query_thread_kernel, 1);
-    } else {
-        if (a.node_fmt == 0) QBVH_LAUNCH(query_warp_kernel, 0);
-        else QBVH_LAUNCH(query_warp_kernel, 1);
+        if (a.node_fmt == 0) launch_thread<0>(a, s);
+        else launch_thread<1>(a, s);
+        return;
     }
-#undef QBVH_LAUNCH
+    const int W = 32 / a.warp_particles;
+    if (a.node_fmt == 0) {
+        if (W == 1) launch_warp<0, 1>(a, s);
+        else if (W == 2) launch_warp<0, 2>(a, s);
+        else launch_warp<0, 4>(a, s);
+    } else {
+        if (W == 1) launch_warp<1, 1>(a, s);
+        else if (W == 2) launch_warp<1, 2>(a, s);
+        else launch_warp<1, 4>(a, s);
+    }
 }
 
 }  // namespace qbvh

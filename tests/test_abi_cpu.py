@@ -88,3 +88,4 @@ def test_package_has_no_cpu_fallback():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "_oracle.so" not in text, f
+

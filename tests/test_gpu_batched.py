@@ -11,7 +11,7 @@ from helpers import assert_same_lists, concat, oracle_list
 pytestmark = pytest.mark.gpu
 
 
-def _batched(systems, n_types=1, cap=256, r=None, traversal=None):
+def _batched(systems, n_types=1, cap=256, r=None, traversal=None, wp=None):
     import torch
 
     from paper_1901_08088_gb300 import NeighborList, _lib
@@ -20,6 +20,8 @@ def _batched(systems, n_types=1, cap=256, r=None, traversal=None):
     nl = NeighborList(0)
     if traversal is not None:
         nl.set_option(_lib.QBVH_OPT_TRAVERSAL, traversal)
+    if wp is not None:
+        nl.set_option(_lib.QBVH_OPT_WARP_PARTICLES, wp)
     nl.build_batched(torch.from_numpy(pos4).cuda(), off, Ls, n_types=n_types)
     nl.query(systems[0].r_list if r is None else r, cap=cap)
     rows, counts = nl.neighbors()
@@ -34,10 +36,10 @@ def _check_systems(systems, rows, counts, off):
         assert_same_lists(rows[a:b] - a, counts[a:b], ro, co)
 
 
-@pytest.mark.parametrize("traversal", [0, 1])
-def test_small_ensemble_matches_oracle_per_system(traversal):
+@pytest.mark.parametrize("traversal,wp", [(0, 32), (1, 32), (1, 16), (1, 8)])
+def test_small_ensemble_matches_oracle_per_system(traversal, wp):
     systems = workloads.batched_ensemble(seed=5, n_sys=12, n_min=250, n_max=3000)
-    rows, counts, off, nl = _batched(systems, traversal=traversal)
+    rows, counts, off, nl = _batched(systems, traversal=traversal, wp=wp)
     _check_systems(systems, rows, counts, off)
     nl.close()
 
@@ -87,10 +89,10 @@ def test_ensemble_with_empty_and_single_particle_systems():
     nl.close()
 
 
-@pytest.mark.parametrize("traversal", [0, 1])
-def test_two_type_batched_systems(traversal):
+@pytest.mark.parametrize("traversal,wp", [(0, 32), (1, 32), (1, 8)])
+def test_two_type_batched_systems(traversal, wp):
     systems = workloads.two_type_lj(seed=8, n_sys=3, n=5000)
-    rows, counts, off, nl = _batched(systems, n_types=2, traversal=traversal)
+    rows, counts, off, nl = _batched(systems, n_types=2, traversal=traversal, wp=wp)
     _check_systems(systems, rows, counts, off)
     nl.close()
 

@@ -20,10 +20,11 @@ def cfg1():
 
 
 @pytest.mark.parametrize("node_format", [0, 1])
-@pytest.mark.parametrize("traversal", [0, 1])
+@pytest.mark.parametrize("traversal,wp", [(0, 32), (1, 32), (1, 16), (1, 8)])
 @pytest.mark.parametrize("bundle,block", [(1, 128), (4, 128), (8, 64), (2, 256), (16, 128)])
-def test_config1_exact_list_equals_bruteforce(cfg1, bundle, block, traversal, node_format):
-    rg, cg, nl, _ = gpu_list(cfg1, bundle=bundle, block=block, traversal=traversal, node_format=node_format)
+def test_config1_exact_list_equals_bruteforce(cfg1, bundle, block, traversal, node_format, wp):
+    rg, cg, nl, _ = gpu_list(cfg1, bundle=bundle, block=block, traversal=traversal, node_format=node_format,
+                             warp_particles=wp)
     ro, co = oracle_list(cfg1, method="brute")
     assert_same_lists(rg, cg, ro, co)
     assert nl.max_count == co.max()
@@ -56,12 +57,12 @@ def _uniform(n, L, r, seed, n_types=1):
                             r_cut=rl.copy())
 
 
-@pytest.mark.parametrize("traversal,node_format", [(0, 0), (1, 0), (1, 1)])
+@pytest.mark.parametrize("traversal,node_format,wp", [(0, 0, 32), (1, 0, 32), (1, 1, 32), (1, 0, 16), (1, 1, 8)])
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 31, 33, 255, 4095, 4097, 12345])
-def test_ragged_sizes(n, traversal, node_format):
+def test_ragged_sizes(n, traversal, node_format, wp):
     L = max(8.0, (n / 0.5) ** (1 / 3))
     s = _uniform(n, L, 2.5, seed=n)
-    rg, cg, nl, _ = gpu_list(s, traversal=traversal, node_format=node_format)
+    rg, cg, nl, _ = gpu_list(s, traversal=traversal, node_format=node_format, warp_particles=wp)
     ro, co = oracle_list(s, method="brute")
     assert_same_lists(rg, cg, ro, co)
     nl.close()
@@ -101,11 +102,11 @@ def test_particles_on_both_faces_of_the_box():
     nl.close()
 
 
-@pytest.mark.parametrize("traversal", [0, 1])
-def test_two_types_per_pair_cutoffs(traversal):
+@pytest.mark.parametrize("traversal,wp", [(0, 32), (1, 32), (1, 16), (1, 8)])
+def test_two_types_per_pair_cutoffs(traversal, wp):
     s = _uniform(20000, 30.0, 1.0, seed=5, n_types=3)
     s.r_list = np.array([[2.0, 2.5, 3.0], [2.5, 1.5, 0.0], [3.0, 0.0, 4.0]], np.float32)
-    rg, cg, nl, _ = gpu_list(s, traversal=traversal)
+    rg, cg, nl, _ = gpu_list(s, traversal=traversal, warp_particles=wp)
     ro, co = oracle_list(s)
     assert_same_lists(rg, cg, ro, co)
     t = nl.tree()
@@ -187,9 +188,9 @@ def test_invalid_inputs_report_errors():
     nl.close()
 
 
-@pytest.mark.parametrize("traversal", [0, 1])
-def test_candidate_mode_is_a_superset_with_few_false_positives(cfg1, traversal):
-    rg, cg, nl, _ = gpu_list(cfg1, candidates=1, cap=512, traversal=traversal)
+@pytest.mark.parametrize("traversal,wp", [(0, 32), (1, 32), (1, 8)])
+def test_candidate_mode_is_a_superset_with_few_false_positives(cfg1, traversal, wp):
+    rg, cg, nl, _ = gpu_list(cfg1, candidates=1, cap=512, traversal=traversal, warp_particles=wp)
     ro, co = oracle_list(cfg1, method="brute")
     sets_o = oracle.rows_as_sets(ro, co)
     sets_g = oracle.rows_as_sets(rg, cg)
@@ -224,10 +225,10 @@ def test_handle_reuse_across_sizes():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("traversal,node_format", [(0, 0), (1, 0), (1, 1)])
-def test_full_size_lj_2m(traversal, node_format):
+@pytest.mark.parametrize("traversal,node_format,wp", [(0, 0, 32), (1, 0, 32), (1, 1, 32), (1, 1, 16)])
+def test_full_size_lj_2m(traversal, node_format, wp):
     s = workloads.workload("lj_n2097152_rho0.8", seed=0)
-    rg, cg, nl, _ = gpu_list(s, traversal=traversal, node_format=node_format)
+    rg, cg, nl, _ = gpu_list(s, traversal=traversal, node_format=node_format, warp_particles=wp)
     ro, co = oracle_list(s)
     rng = np.random.default_rng(0)
     idx = np.sort(rng.choice(s.n, 8192, replace=False))
