@@ -438,8 +438,16 @@ def run_grid_comparison(args, local):
 
             start = {k: v[0] for k, v in space.items()}
             best, ms, _ = autotune.tune(step, space=space, start=start, reps=5, warmup=2, sweeps=1)
-            res["bvh_ms" if method == 0 else "grid_ms"] = ms
-            res["bvh_options" if method == 0 else "grid_options"] = autotune.option_names(best)
+            tag = "bvh" if method == 0 else "grid"
+            res[f"{tag}_ms"] = ms
+            res[f"{tag}_options"] = autotune.option_names(best)
+            # split: build alone, then query alone (async enqueue + one wait)
+            for k, v in best.items():
+                nl.set_option(k, v)
+            res[f"{tag}_build_ms"] = autotune.time_step(lambda o: nl.build(pos4, s.L), {}, reps=5, warmup=2)
+            nl.build(pos4, s.L)
+            res[f"{tag}_query_ms"] = autotune.time_step(lambda o: nl.query_async(s.r_list, CAP), {}, reps=5,
+                                                        warmup=2)
             nl.close()
         res["bvh_speedup_over_grid"] = res["grid_ms"] / res["bvh_ms"]
         out.append(res)

@@ -251,14 +251,6 @@ int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *of
     if (rc) return rc;
     rc = upload_if_changed(h, h->sys_off, h->up_off, h->off, s);
     if (rc) return rc;
-    if (n > 0) {
-        // parents start at -1 so that a missing link ends a walk instead of
-        // sending it to an arbitrary index
-        if (cudaMemsetAsync(h->visit.p, 0, (size_t)n * 4, s) != cudaSuccess ||
-            cudaMemsetAsync(h->par_int.p, 0xFF, (size_t)n * 4, s) != cudaSuccess ||
-            cudaMemsetAsync(h->par_leaf.p, 0xFF, (size_t)n * 4, s) != cudaSuccess)
-            return QBVH_ERR_CUDA;
-    }
 
     BuildArgs a;
     memset(&a, 0, sizeof a);
@@ -286,6 +278,9 @@ int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *of
     a.nodes32 = h->node_fmt == 1 ? reinterpret_cast<float4 *>(h->nodes32.p) : nullptr;
     a.leaves = reinterpret_cast<float4 *>(h->leaves.p);
     a.status = reinterpret_cast<DevStatus *>(h->status.p);
+    a.sort_scratch = reinterpret_cast<unsigned *>(h->sort_scratch.p);
+    a.sort_scratch_words = sort_scratch_bytes(n, passes) / sizeof(unsigned);
+    a.sort_passes = passes;
     h->built_fmt = h->node_fmt;
 
     launch_build_prepare(a, s);
@@ -293,7 +288,7 @@ int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *of
     launch_seg_scan(a, s);
     h->sorted = radix_sort_pairs(h->wide, h->keys[0].p, h->keys[1].p, reinterpret_cast<int *>(h->vals[0].p),
                                  reinterpret_cast<int *>(h->vals[1].p), n, bits, h->sort_scratch.p,
-                                 &a.status->err, s);
+                                 &a.status->err, s, /*prepared=*/true);
     a.keys_sorted = h->keys[h->sorted].p;
     a.order = reinterpret_cast<const int *>(h->vals[h->sorted].p);
     launch_karras(a, s);

@@ -64,11 +64,15 @@ __device__ __forceinline__ int sys_of(const int *off, int n_sys, int i)
 // IEEE floats equals the order of their bit patterns as unsigned integers.
 __device__ __forceinline__ unsigned acc_init(int f) { return (f >= 1 && f <= 3) ? 0x7F800000u : 0u; }
 
-__global__ void prepare_kernel(unsigned *acc, int n_seg, DevStatus *status)
+// Resets the per-tree accumulators, the status word and the radix-sort scratch
+// (histograms, tickets, look-back words) in one grid-stride pass.
+__global__ void prepare_kernel(unsigned *acc, int n_seg, DevStatus *status, unsigned *scratch, size_t words)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n_seg * 8) acc[t] = acc_init(t & 7);
-    if (t == 0) {
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t t = t0; t < (size_t)n_seg * 8; t += stride) acc[t] = acc_init((int)(t & 7));
+    for (size_t t = t0; t < words; t += stride) scratch[t] = 0u;
+    if (t0 == 0) {
         status->max_count = 0;
         status->err = 0u;
     }
@@ -78,9 +82,19 @@ template <bool WIDE>
 __global__ void __launch_bounds__(kBlock) morton_kernel(const BuildArgs a, unsigned *acc)
 {
     __shared__ unsigned s_acc[kLocalSegs * 8];
+    __shared__ unsigned s_hist[8 * 256];
     __shared__ int s_seg0, s_span;
     const int i = blockIdx.x * kBlock + threadIdx.x;
     const int T = a.n_types;
+    const int npass = a.sort_passes;
+    for (int t = threadIdx.x; t < npass * 256; t += kBlock) s_hist[t] = 0u;
+    if (i < a.n) {
+        // fresh arrival counters and parent links for the fit (a missing link
+        // ends a walk instead of sending it to an arbitrary index)
+        a.visit[i] = 0;
+        a.par_int[i] = -1;
+        a.par_leaf[i] = -1;
+    }
     if (threadIdx.x == 0) {
         int first = blockIdx.x * kBlock;
         int last = min(first + kBlock, a.n) - 1;
@@ -120,11 +134,14 @@ __global__ void __launch_bounds__(kBlock) morton_kernel(const BuildArgs a, unsig
                               (spread10(bin_of(p.y, sy.mscale)) << 1) |
                               spread10(bin_of(p.z, sy.mscale));
         seg = k * T + type;
+        const unsigned long long key = WIDE ? (((unsigned long long)seg << 30) | code)
+                                            : (unsigned long long)(((unsigned)type << 30) | code);
         if (WIDE)
-            reinterpret_cast<unsigned long long *>(a.keys)[i] =
-                ((unsigned long long)seg << 30) | code;
+            reinterpret_cast<unsigned long long *>(a.keys)[i] = key;
         else
-            reinterpret_cast<unsigned *>(a.keys)[i] = ((unsigned)type << 30) | code;
+            reinterpret_cast<unsigned *>(a.keys)[i] = (unsigned)key;
+        // digit histograms of the key sort, one per 8-bit pass
+        for (int p = 0; p < npass; ++p) atomicAdd(&s_hist[p * 256 + (unsigned)((key >> (8 * p)) & 255u)], 1u);
     }
     if (err) atomicOr(&a.status->err, err);
 
@@ -157,8 +174,10 @@ __global__ void __launch_bounds__(kBlock) morton_kernel(const BuildArgs a, unsig
         for (int f = 1; f <= 3; ++f) atomicMin(dst_base + f, v[f]);
         for (int f = 4; f <= 6; ++f) atomicMax(dst_base + f, v[f]);
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < npass * 256; t += kBlock)
+        if (s_hist[t]) atomicAdd(a.sort_scratch + t, s_hist[t]);   // histograms lead the scratch
     if (local) {
-        __syncthreads();
         for (int t = threadIdx.x; t < s_span * 8; t += kBlock) {
             const int f = t & 7;
             const unsigned x = s_acc[t];
@@ -457,8 +476,11 @@ inline int blocks_for(int n, int b) { return (n + b - 1) / b; }
 
 void launch_build_prepare(const BuildArgs &a, cudaStream_t s)
 {
-    const int work = a.n_seg * 8 > 1 ? a.n_seg * 8 : 1;
-    prepare_kernel<<<blocks_for(work, kBlock), kBlock, 0, s>>>(a.seg_rootbits, a.n_seg, a.status);
+    const size_t work = (size_t)a.n_seg * 8 > a.sort_scratch_words ? (size_t)a.n_seg * 8 : a.sort_scratch_words;
+    int blocks = (int)((work + kBlock - 1) / kBlock);
+    blocks = blocks < 1 ? 1 : (blocks > 1216 ? 1216 : blocks);
+    prepare_kernel<<<blocks, kBlock, 0, s>>>(a.seg_rootbits, a.n_seg, a.status, a.sort_scratch,
+                                             a.sort_scratch_words);
 }
 
 void launch_morton(const BuildArgs &a, cudaStream_t s)

@@ -76,6 +76,9 @@ struct BuildArgs {
     const int *sys_off;  // [n_sys + 1]
     SegInfo *seg;        // [n_seg]
     unsigned *seg_rootbits; // [n_seg * 8] per-tree count and root AABB accumulators
+    unsigned *sort_scratch;  // radix-sort scratch: histograms, tickets, look-back words
+    size_t sort_scratch_words;
+    int sort_passes;         // digit passes of the key sort
     int *seg_start;      // [n_seg + 1]
     float *frames;       // [n_seg * 8]
     void *keys;          // morton keys, input of the sort
@@ -113,7 +116,7 @@ size_t sort_scratch_bytes(int n, int passes);
 // holds the input keys; values start as 0..n-1.  Returns the index (0 or 1)
 // of the buffer pair holding the result: 0 -> (keys_a, vals_a), 1 -> (keys_b, vals_b).
 int radix_sort_pairs(bool wide, void *keys_a, void *keys_b, int *vals_a, int *vals_b, int n,
-                     int bits, void *scratch, unsigned *err, cudaStream_t s);
+                     int bits, void *scratch, unsigned *err, cudaStream_t s, bool prepared = false);
 int sort_wait_selftest(int spin_limit, unsigned *err_out, cudaStream_t s);
 
 // ---- traversal (query.cu) ------------------------------------------------

@@ -7,9 +7,10 @@
 // so that the particle order is deterministic (Sec. 3).
 //
 // Kernels:
-//   hist  : one read of the keys, 256-bin histograms of every digit
-//   scan  : exclusive scan of each histogram -> global bucket starts
-//   pass  : one per digit; tiles of 4096 keys are taken in ticket order, so a
+//   hist  : one read of the keys, 256-bin histograms of every digit (the
+//           build computes them in its Morton pass instead)
+//   pass  : one per digit; tile 0 scans the digit histogram into global bucket
+//           starts; tiles of keys are taken in ticket order, so a
 //           tile only ever waits for tiles whose blocks are already running.
 //           The wait is bounded: after kSpinLimit polls the block records
 //           QBVH_DEVERR_TIMEOUT in the error word and continues (the result is
@@ -89,16 +90,6 @@ __device__ __forceinline__ unsigned block_excl_scan256(unsigned v, unsigned *s_w
     return before + x - v;
 }
 
-__global__ void __launch_bounds__(kThreads) scan_kernel(unsigned *hist, int npass)
-{
-    __shared__ unsigned s_warp[kWarps];
-    for (int p = 0; p < npass; ++p) {
-        unsigned v = hist[p * kRadix + threadIdx.x];
-        unsigned e = block_excl_scan256(v, s_warp);
-        hist[p * kRadix + threadIdx.x] = e;
-    }
-}
-
 template <typename K>
 __global__ void __launch_bounds__(kThreads) pass_kernel(const K *__restrict__ kin, const int *__restrict__ vin,
                                                         K *__restrict__ kout, int *__restrict__ vout, int n,
@@ -120,6 +111,9 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(const K *__restrict__ ki
     __syncthreads();
     const int tile = (int)s_misc[0];
     const int base = tile * kTile + warp * (32 * kItems);
+    // tile 0 turns the pass's digit histogram into global bucket starts
+    unsigned bucket_start = 0u;
+    if (tile == 0) bucket_start = block_excl_scan256(bucket_base[tid], s_misc + 1);
 
     K key[kItems];
     int val[kItems];
@@ -159,7 +153,7 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(const K *__restrict__ ki
         unsigned *mine = status + (size_t)tile * kRadix + d;
         unsigned excl;
         if (tile == 0) {
-            excl = bucket_base[d];
+            excl = bucket_start;   // this digit's global start
             st_relaxed(mine, kFlagPre | (excl + cnt));
         } else {
             st_relaxed(mine, kFlagAgg | cnt);
@@ -218,18 +212,21 @@ size_t pass_smem()
 }
 
 template <typename K>
-int sort_impl(K *ka, K *kb, int *va, int *vb, int n, int bits, void *scratch, unsigned *err, cudaStream_t s)
+int sort_impl(K *ka, K *kb, int *va, int *vb, int n, int bits, void *scratch, unsigned *err, bool prepared,
+              cudaStream_t s)
 {
     const int npass = (bits + 7) / 8;
     const int tiles = sort_num_tiles(n);
     unsigned *hist = reinterpret_cast<unsigned *>(scratch);
     unsigned *ticket = hist + kMaxPasses * kRadix;
     unsigned *status = ticket + kMaxPasses * 4;
-    cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, npass), s);
-    int hb = (n + kThreads * 8 - 1) / (kThreads * 8);
-    hb = hb < 1 ? 1 : (hb > 1216 ? 1216 : hb);
-    hist_kernel<K><<<hb, kThreads, 0, s>>>(ka, n, npass, hist);
-    scan_kernel<<<1, kThreads, 0, s>>>(hist, npass);
+    if (!prepared) {
+        // zeroed scratch and digit histograms, unless the caller's kernels made them
+        cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, npass), s);
+        int hb = (n + kThreads * 8 - 1) / (kThreads * 8);
+        hb = hb < 1 ? 1 : (hb > 1216 ? 1216 : hb);
+        hist_kernel<K><<<hb, kThreads, 0, s>>>(ka, n, npass, hist);
+    }
     static bool attr_set = false;
     const size_t smem = pass_smem<K>();
     if (!attr_set) {
@@ -293,7 +290,7 @@ int sort_wait_selftest(int spin_limit, unsigned *err_out, cudaStream_t s)
     const size_t smem = pass_smem<unsigned>();
     cudaFuncSetAttribute(pass_kernel<unsigned>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     pass_kernel<unsigned><<<1, kThreads, smem, s>>>(kin, nullptr, kout, vout, n, 0, base, status, ticket, err,
-                                                    spin_limit);
+                                                    spin_limit);   // tile 1: never scans
     cudaMemcpyAsync(err_out, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
     const cudaError_t e = cudaStreamSynchronize(s);
     cudaFree(kin);
@@ -304,15 +301,15 @@ int sort_wait_selftest(int spin_limit, unsigned *err_out, cudaStream_t s)
 }
 
 int radix_sort_pairs(bool wide, void *keys_a, void *keys_b, int *vals_a, int *vals_b, int n, int bits,
-                     void *scratch, unsigned *err, cudaStream_t s)
+                     void *scratch, unsigned *err, cudaStream_t s, bool prepared)
 {
     if (n <= 0) return 0;
     if (wide)
         return sort_impl<unsigned long long>(reinterpret_cast<unsigned long long *>(keys_a),
                                              reinterpret_cast<unsigned long long *>(keys_b), vals_a, vals_b, n,
-                                             bits, scratch, err, s);
+                                             bits, scratch, err, prepared, s);
     return sort_impl<unsigned>(reinterpret_cast<unsigned *>(keys_a), reinterpret_cast<unsigned *>(keys_b), vals_a,
-                               vals_b, n, bits, scratch, err, s);
+                               vals_b, n, bits, scratch, err, prepared, s);
 }
 
 }  // namespace qbvh
