@@ -37,6 +37,7 @@ constexpr unsigned kFlagPre = 2u << 30;
 constexpr unsigned kValMask = (1u << 30) - 1u;
 constexpr int kMaxPasses = 8;
 constexpr int kSpinLimit = 1 << 20;
+constexpr int kLookBatch = 8;
 
 __device__ __forceinline__ void st_relaxed(unsigned *p, unsigned v)
 {
@@ -160,20 +161,33 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(const K *__restrict__ ki
             excl = 0u;
             int j = tile - 1;
             int spins = 0;
-            while (true) {
-                const unsigned v = ld_relaxed(status + (size_t)j * kRadix + d);
-                const unsigned f = v & ~kValMask;
-                if (f == 0u) {
+            bool done = false;
+            // predecessors are read kLookBatch at a time (independent loads)
+            // and consumed newest first: aggregates add up until an inclusive
+            // prefix ends the walk; an unpublished slot is polled again
+            while (!done) {
+                unsigned v[kLookBatch];
+#pragma unroll
+                for (int b = 0; b < kLookBatch; ++b)
+                    v[b] = (j - b >= 0) ? ld_relaxed(status + (size_t)(j - b) * kRadix + d) : kFlagPre;
+#pragma unroll
+                for (int b = 0; b < kLookBatch; ++b) {
+                    if (done) break;
+                    const unsigned f = v[b] & ~kValMask;
+                    if (f == 0u) break;           // not yet published: poll from here
+                    excl += v[b] & kValMask;      // kFlagPre past tile 0 carries value 0
+                    --j;
+                    if (f == kFlagPre || j < 0) done = true;
+                }
+                if (done) break;
+                const unsigned f0 = ld_relaxed(status + (size_t)j * kRadix + d) & ~kValMask;
+                if (f0 == 0u) {
                     if (++spins > spin_limit) {
                         atomicOr(err, QBVH_DEVERR_TIMEOUT);
                         break;
                     }
                     if (spins > 64) __nanosleep(100);
-                    continue;
                 }
-                excl += v & kValMask;
-                if (f == kFlagPre || j == 0) break;
-                --j;
             }
             st_relaxed(mine, kFlagPre | ((excl + cnt) & kValMask));
         }
