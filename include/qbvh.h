@@ -84,8 +84,9 @@ int qbvh_destroy(qbvh_handle h);
  * paper's one-particle leaves.  Values 1..32, default 16.  Takes effect at
  * the next build. */
 #define QBVH_OPT_BUNDLE 1
-/* Threads per block of the traversal kernel: 32..1024, multiple of 32,
- * default 128.  Takes effect at the next query. */
+/* Threads per block of the traversal kernel: 32..256, multiple of 32,
+ * default 128 (the warp walk is compiled for at most 256 threads per block
+ * so that 8 blocks fit on an SM).  Takes effect at the next query. */
 #define QBVH_OPT_QUERY_BLOCK 2
 /* 1 = skip the exact leaf test and list every particle whose node the search
  * sphere overlaps, as Alg. 1 does (candidates, false positives included).

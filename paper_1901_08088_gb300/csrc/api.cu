@@ -516,7 +516,7 @@ int qbvh_set_option(qbvh_handle h, int option, int value)
         h->bundle_k = value;
         return QBVH_OK;
     case QBVH_OPT_QUERY_BLOCK:
-        if (value < 32 || value > 1024 || (value & 31)) return QBVH_ERR_INVALID_ARG;
+        if (value < 32 || value > 256 || (value & 31)) return QBVH_ERR_INVALID_ARG;
         h->query_block = value;
         return QBVH_OK;
     case QBVH_OPT_CANDIDATES:

@@ -172,11 +172,53 @@ struct Query {
     float rl2;
 };
 
-// The exact test of leaf j under the current image (see the header comment).
+// Packed FP32 pairs (sub/mul .rn.f32x2, sm_100 and later): each half is one
+// IEEE round-to-nearest operation, so a pair gives exactly the two scalar
+// results.  A leaf's (x, y) already lies in an aligned register pair after
+// its 16-byte load, which makes the packing free.
+#ifndef QBVH_F32X2
+#define QBVH_F32X2 1
+#endif
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2_pack(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// d2 of the exact test (see the header comment) for leaf position q.
 // SHIFT = false is the zero image, where subtracting n L = 0 is the identity.
 template <bool SHIFT>
-__device__ __forceinline__ void exact_leaf(const Query &c, Row &out, int j, const float4 q)
+__device__ __forceinline__ float exact_d2(const Query &c, const float4 q)
 {
+#if QBVH_F32X2
+    f32x2 dxy = f2_sub(f2_pack(q.x, q.y), f2_pack(c.xi, c.yi));
+    float dz = __fsub_rn(q.z, c.zi);
+    if (SHIFT) {
+        dxy = f2_sub(dxy, f2_pack(c.nLx, c.nLy));
+        dz = __fsub_rn(dz, c.nLz);
+    }
+    float sx, sy;
+    f2_unpack(f2_mul(dxy, dxy), sx, sy);
+    return __fadd_rn(__fadd_rn(sx, sy), __fmul_rn(dz, dz));
+#else
     float dx = __fsub_rn(q.x, c.xi);
     float dy = __fsub_rn(q.y, c.yi);
     float dz = __fsub_rn(q.z, c.zi);
@@ -185,8 +227,15 @@ __device__ __forceinline__ void exact_leaf(const Query &c, Row &out, int j, cons
         dy = __fsub_rn(dy, c.nLy);
         dz = __fsub_rn(dz, c.nLz);
     }
-    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-    if (d2 < c.rl2 && j != c.self) out.push(__float_as_int(q.w) & 0x7FFFFFFF);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+#endif
+}
+
+// The exact test of leaf j under the current image.
+template <bool SHIFT>
+__device__ __forceinline__ void exact_leaf(const Query &c, Row &out, int j, const float4 q)
+{
+    if (exact_d2<SHIFT>(c, q) < c.rl2 && j != c.self) out.push(__float_as_int(q.w) & 0x7FFFFFFF);
 }
 
 // Alg. 1 without the exact filter: list j when the sphere overlaps its
@@ -215,16 +264,7 @@ __device__ __forceinline__ bool leaf_accepts(const QueryArgs &A, const Query &c,
 {
     if (j == c.self) return false;
     if (CAND) return overlap_q(c.px, c.py, c.pz, __ldg(A.leaf_q + j), f, rs2);
-    float dx = __fsub_rn(q.x, c.xi);
-    float dy = __fsub_rn(q.y, c.yi);
-    float dz = __fsub_rn(q.z, c.zi);
-    if (SHIFT) {
-        dx = __fsub_rn(dx, c.nLx);
-        dy = __fsub_rn(dy, c.nLy);
-        dz = __fsub_rn(dz, c.nLz);
-    }
-    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-    return d2 < c.rl2;
+    return exact_d2<SHIFT>(c, q) < c.rl2;
 }
 
 // Append for W lanes sharing a row: the lanes of one particle are `same`

@@ -21,7 +21,7 @@ def cfg1():
 
 @pytest.mark.parametrize("node_format", [0, 1])
 @pytest.mark.parametrize("traversal,wp", [(0, 32), (1, 32), (1, 16), (1, 8)])
-@pytest.mark.parametrize("bundle,block", [(1, 128), (4, 128), (8, 64), (2, 256), (16, 128)])
+@pytest.mark.parametrize("bundle,block", [(1, 128), (4, 128), (8, 64), (2, 256), (16, 128), (32, 32)])
 def test_config1_exact_list_equals_bruteforce(cfg1, bundle, block, traversal, node_format, wp):
     rg, cg, nl, _ = gpu_list(cfg1, bundle=bundle, block=block, traversal=traversal, node_format=node_format,
                              warp_particles=wp)
@@ -185,6 +185,9 @@ def test_invalid_inputs_report_errors():
     nl.build(torch.from_numpy(workloads.pack_float4(s.pos, s.types)).cuda(), s.L)
     assert nl.query(5.0, raise_on_error=False) == _lib.QBVH_ERR_CUTOFF_TOO_LARGE
     assert nl.query(2.0, raise_on_error=False) == _lib.QBVH_OK
+    # the traversal kernels are compiled for at most 256 threads per block
+    assert _lib.lib().qbvh_set_option(nl.h, _lib.QBVH_OPT_QUERY_BLOCK, 512) == _lib.QBVH_ERR_INVALID_ARG
+    assert _lib.lib().qbvh_set_option(nl.h, _lib.QBVH_OPT_QUERY_BLOCK, 48) == _lib.QBVH_ERR_INVALID_ARG
     nl.close()
 
 
