@@ -172,37 +172,6 @@ struct Query {
     float rl2;
 };
 
-// Packed FP32 pairs (sub/mul .rn.f32x2, sm_100 and later): each half is one
-// IEEE round-to-nearest operation, so a pair gives exactly the two scalar
-// results.  A leaf's (x, y) already lies in an aligned register pair after
-// its 16-byte load, which makes the packing free.
-#ifndef QBVH_F32X2
-#define QBVH_F32X2 1
-#endif
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 f2_pack(float lo, float hi)
-{
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void f2_unpack(f32x2 v, float &lo, float &hi)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b)
-{
-    f32x2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b)
-{
-    f32x2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-
 // d2 of the exact test (see the header comment) for leaf position q.
 // SHIFT = false is the zero image, where subtracting n L = 0 is the identity.
 template <bool SHIFT>
@@ -446,6 +415,64 @@ __global__ void query_thread_kernel(const __grid_constant__ QueryArgs a)
     warp_max_count(my_count, a.status);
 }
 
+// Bundles that few lanes overlap.  Every lane testing every leaf costs the
+// warp one trip per leaf however few lanes overlap the bundle box.  Instead,
+// the overlapping lanes' tests are spread over the warp: the bundle's leaves
+// go to S = 16 (or 32) consecutive lanes, loaded once, and each trip serves
+// 32 / S overlapping particles, whose centre, row and count come by shuffle.
+// A particle's accepted leaves are packed in leaf order, so rows are the same
+// as with the per-lane loop.  Every lane of the warp calls this together;
+// `hm` (warp-uniform) holds the overlapping lanes, cnt <= 32 leaves.
+// Used when at most QBVH_SPREAD_MAX lanes overlap (N = 2M, density 0.8,
+// K = 16; query ms by threshold: 0: 2.15, 4: 2.09, 8: 2.05, 12: 1.99,
+// 16: 1.97, 20: 2.04, 32: 2.42).
+#ifndef QBVH_SPREAD_MAX
+#define QBVH_SPREAD_MAX 16
+#endif
+template <bool SHIFT>
+__device__ __forceinline__ void bundle_spread(const QueryArgs &a, const Query &c, Row &out, int first, int cnt,
+                                              unsigned hm)
+{
+    const int lane = threadIdx.x & 31;
+    const bool wide = cnt > 16;               // warp-uniform
+    const int half = wide ? 0 : (lane >> 4);  // which particle of the trip this lane serves
+    const int k = wide ? lane : (lane & 15);  // leaf slot
+    const int j = first + k;
+    const bool jv = k < cnt;
+    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (jv) q = __ldg(a.leaves + j);
+    const int id = __float_as_int(q.w) & 0x7FFFFFFF;
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    const unsigned gmask = wide ? 0xFFFFFFFFu : (half ? 0xFFFF0000u : 0x0000FFFFu);
+    while (hm) {
+        const int o0 = __ffs(hm) - 1;
+        hm &= hm - 1u;
+        int o1 = -1;
+        if (!wide && hm) {
+            o1 = __ffs(hm) - 1;
+            hm &= hm - 1u;
+        }
+        const int owner = half ? o1 : o0;
+        const int src = owner < 0 ? lane : owner;
+        Query t = c;
+        t.xi = __shfl_sync(FULL, c.xi, src);
+        t.yi = __shfl_sync(FULL, c.yi, src);
+        t.zi = __shfl_sync(FULL, c.zi, src);
+        t.self = c.self - lane + src;
+        const int ocount = __shfl_sync(FULL, out.count, src);
+        int *orow = reinterpret_cast<int *>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(out.row), src));
+        const bool acc = owner >= 0 && jv && exact_d2<SHIFT>(t, q) < c.rl2 && j != t.self;
+        const unsigned m = __ballot_sync(FULL, acc);
+        if (acc) {
+            const int slot = ocount + __popc(m & gmask & lt);
+            if (slot < out.cap) __stcs(orow + slot, id);
+        }
+        if (lane == o0) out.count += __popc(m & (wide ? 0xFFFFFFFFu : 0x0000FFFFu));
+        if (lane == o1) out.count += __popc(m & 0xFFFF0000u);
+    }
+}
+
 // Registers are capped so that 8 blocks of 256 threads (64 warps) fit on an
 // SM: the walk is latency-bound and more resident warps hide more of it
 // (measured 2.37 -> 2.23 ms at N = 2M despite a few spilled bytes).
@@ -475,7 +502,8 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
         if (node >= 0) {
             const Node nd = decode<FMT>(load_raw<FMT>(a, node), f);
             const bool hit = overlap(c.px, c.py, c.pz, nd, lrs2);
-            if (__any_sync(FULL, hit)) {
+            const unsigned hm = __ballot_sync(FULL, hit);
+            if (hm) {
                 if (nd.bundle) {
                     int l = bundle_last(nd, last);
                     if (nd.left < g.start || l > last) {
@@ -483,7 +511,9 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                         l = nd.left - 1;
                     }
                     int j = nd.left;
-                    if (W == 1) {
+                    if (W == 1 && !CAND && l - j < 32 && __popc(hm) <= QBVH_SPREAD_MAX) {
+                        bundle_spread<SHIFT>(a, c, out, j, l - j + 1, hm);
+                    } else if (W == 1) {
 #if QBVH_LEAF_PAIRS
                         for (; j < l; j += 2) {   // two leaves per step: two loads in flight
                             const float4 q0 = __ldg(a.leaves + j);
