@@ -101,30 +101,41 @@ class ClockSampler:
 
 
 # DRAM bytes (read + write) of one traversal launch at N = 2,097,152, measured with
-# ncu (profiles/query_warp_kernel_lj_n2097152.md) for the options below and the
-# traversal source whose SHA-256 prefix is given; any other source or options
+# ncu (profiles/query_warp_kernel_lj_n2097152.md) for the options of each entry and
+# the traversal sources whose SHA-256 prefix is given; any other source or options
 # report null.
 PROFILED_TRAFFIC = {
-    "query_sha256": "525433449c765e13",
-    "options": {"bundle_k": 16, "node_format": 1, "traversal": 1, "query_block": 256},
-    "bytes": 436.74e6 + 1.27e9,
+    "source_sha256": "",
+    "entries": [],
 }
+# kernels of one timed step: build = prepare, Morton (+ sort histograms), segment
+# scan, 4 onesweep passes (30-bit keys, 8-bit digits), Karras, fit; query = 2
+# traversal launches (zero image, other images); LJ = forward + fixed-order FP64 finalize
+KERNELS_PER_STEP = 9 + 2 + 2
+_TRAFFIC_SOURCES = ("paper_1901_08088_gb300/csrc/query.cu", "paper_1901_08088_gb300/csrc/qbvh_internal.cuh")
+
+
+def traversal_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in _TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def _profiled_traffic(opts: dict, n: int):
-    import hashlib
-
-    src = os.path.join(ROOT, "paper_1901_08088_gb300", "csrc", "query.cu")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = traversal_source_hash()
     except OSError:
         return None
-    want = PROFILED_TRAFFIC
-    if n != 2_097_152 or sha != want["query_sha256"]:
+    if n != 2_097_152 or sha != PROFILED_TRAFFIC["source_sha256"]:
         return None
-    if any(opts.get(k) != v for k, v in want["options"].items()):
-        return None
-    return want["bytes"]
+    for e in PROFILED_TRAFFIC["entries"]:
+        if all(opts.get(k) == v for k, v in e["options"].items()):
+            return e["bytes"]
+    return None
 
 
 def max_over_ranks(x: float) -> float:
@@ -319,7 +330,7 @@ def run_ours(args):
             },
             "e2e": {"value": world * n * e2e_steps / (e2e_ms * 1e-3), "unit": "particles/s",
                     "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 12 * n + 8},
-            "gpu_launches": args.steps * 14,
+            "gpu_launches": args.steps * KERNELS_PER_STEP,
             "autotune": {"evaluations": tune_evals, "chosen": autotune.option_names(
                 {k: nl.get_option(k) for k in autotune.OPTION_SPACE})},
             "clocks": clocks,

@@ -104,6 +104,60 @@ __device__ __forceinline__ Node decode_f(const float4 a, const float4 b)
     return n;
 }
 
+// Read-only loads of tree words (nodes, leaves).  QBVH_TREE_EVICT_LAST = 1
+// marks them evict-last in L2, so that the list writes streaming through L2
+// (about 1.4 GB of DRAM writes per launch at N = 2M, against a 96 MB tree)
+// evict them after everything else: query 1.92 -> 1.84 ms at N = 2M.
+// QBVH_NODE_V8 = 1 reads a 32-byte FP32 node with one 256-bit load (sm_100
+// and later) instead of two 128-bit ones (same speed, one instruction).
+#ifndef QBVH_TREE_EVICT_LAST
+#define QBVH_TREE_EVICT_LAST 1
+#endif
+#ifndef QBVH_NODE_V8
+#define QBVH_NODE_V8 1
+#endif
+__device__ __forceinline__ float4 tree_ld(const float4 *p)
+{
+#if QBVH_TREE_EVICT_LAST
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    float4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol));
+    return v;
+#else
+    return __ldg(p);
+#endif
+}
+__device__ __forceinline__ int4 tree_ld(const int4 *p)
+{
+#if QBVH_TREE_EVICT_LAST
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    int4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(pol));
+    return v;
+#else
+    return __ldg(p);
+#endif
+}
+// both halves of a 32-byte FP32 node (32-byte aligned: node arrays come from
+// the allocator's 256-byte aligned blocks)
+__device__ __forceinline__ void node32_ld(const float4 *p, float4 &a, float4 &b)
+{
+#if QBVH_NODE_V8 && QBVH_TREE_EVICT_LAST
+    asm("ld.global.nc.L2::evict_last.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w) : "l"(p));
+#elif QBVH_NODE_V8
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w) : "l"(p));
+#else
+    a = tree_ld(p);
+    b = tree_ld(p + 1);
+#endif
+}
+
 // Raw words of a node, loaded ahead of use.
 struct Raw {
     int4 q;
@@ -115,10 +169,9 @@ __device__ __forceinline__ Raw load_raw(const QueryArgs &A, int id)
 {
     Raw r;
     if (FMT == 0) {
-        r.q = __ldg(A.nodes + id);
+        r.q = tree_ld(A.nodes + id);
     } else {
-        r.a = __ldg(A.nodes32 + 2 * (size_t)id);
-        r.b = __ldg(A.nodes32 + 2 * (size_t)id + 1);
+        node32_ld(A.nodes32 + 2 * (size_t)id, r.a, r.b);
     }
     return r;
 }
@@ -170,6 +223,22 @@ __device__ __forceinline__ bool overlap_q(float px, float py, float pz, uint2 q,
     return overlap(px, py, pz, n, rs2);
 }
 
+// Store of one list entry.  QBVH_ROW_STORE: 0 = streaming (evict-first),
+// 1 = cache at L2 (.cg), 2 = default write-back.
+#ifndef QBVH_ROW_STORE
+#define QBVH_ROW_STORE 0
+#endif
+__device__ __forceinline__ void row_store(int *p, int v)
+{
+#if QBVH_ROW_STORE == 0
+    __stcs(p, v);
+#elif QBVH_ROW_STORE == 1
+    __stcg(p, v);
+#else
+    *p = v;
+#endif
+}
+
 // Row writer.  Entries past cap are counted, not written.  The list is never
 // read back by the traversal, so it is stored with the streaming (evict-first)
 // hint and does not push the tree out of L2.  (Gathering four entries into
@@ -182,7 +251,7 @@ struct Row {
 
     __device__ __forceinline__ void push(int j)
     {
-        if (count < cap) __stcs(row + count, j);
+        if (count < cap) row_store(row + count, j);
         ++count;
     }
 };
@@ -269,7 +338,7 @@ __device__ __forceinline__ void push_shared(Row &out, bool acc, int j, unsigned 
         unsigned lt;
         asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
         const int slot = out.count + __popc(m & lt);
-        if (slot < out.cap) __stcs(out.row + slot, j);
+        if (slot < out.cap) row_store(out.row + slot, j);
     }
     out.count += __popc(m);
 }
@@ -415,7 +484,7 @@ __global__ void query_thread_kernel(const __grid_constant__ QueryArgs a)
                                     l = nd.left - 1;
                                 }
                                 for (int j = nd.left; j <= l; ++j)
-                                    test_leaf<CAND>(a, c, out, j, __ldg(a.leaves + j), f, rs2);
+                                    test_leaf<CAND>(a, c, out, j, tree_ld(a.leaves + j), f, rs2);
                                 node = nd.rope;
                             } else {
                                 node = nd.left;
@@ -425,7 +494,7 @@ __global__ void query_thread_kernel(const __grid_constant__ QueryArgs a)
                         }
                     } else {
                         const int j = ~node;
-                        const float4 q = __ldg(a.leaves + j);
+                        const float4 q = tree_ld(a.leaves + j);
                         test_leaf<CAND>(a, c, out, j, q, f, rs2);
                         node = (j == last) ? QBVH_END : ((__float_as_int(q.w) < 0) ? j + 1 : ~(j + 1));
                     }
@@ -463,7 +532,7 @@ __device__ __forceinline__ void bundle_spread(const QueryArgs &a, const Query &c
     const int j = first + k;
     const bool jv = k < cnt;
     float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (jv) q = __ldg(a.leaves + j);
+    if (jv) q = tree_ld(a.leaves + j);
     const int id = __float_as_int(q.w) & 0x7FFFFFFF;
     unsigned lt;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
@@ -489,7 +558,7 @@ __device__ __forceinline__ void bundle_spread(const QueryArgs &a, const Query &c
         const unsigned m = __ballot_sync(FULL, acc);
         if (acc) {
             const int slot = ocount + __popc(m & gmask & lt);
-            if (slot < out.cap) __stcs(orow + slot, id);
+            if (slot < out.cap) row_store(orow + slot, id);
         }
         if (lane == o0) out.count += __popc(m & (wide ? 0xFFFFFFFFu : 0x0000FFFFu));
         if (lane == o1) out.count += __popc(m & 0xFFFF0000u);
@@ -539,8 +608,8 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                     } else if (W == 1) {
 #if QBVH_LEAF_PAIRS
                         for (; j < l; j += 2) {   // two leaves per step: two loads in flight
-                            const float4 q0 = __ldg(a.leaves + j);
-                            const float4 q1 = __ldg(a.leaves + j + 1);
+                            const float4 q0 = tree_ld(a.leaves + j);
+                            const float4 q1 = tree_ld(a.leaves + j + 1);
                             if (on) {
                                 test_leaf<CAND, SHIFT>(a, c, out, j, q0, f, rs2);
                                 test_leaf<CAND, SHIFT>(a, c, out, j + 1, q1, f, rs2);
@@ -548,7 +617,7 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                         }
 #endif
                         for (; j <= l; ++j) {
-                            const float4 q = __ldg(a.leaves + j);
+                            const float4 q = tree_ld(a.leaves + j);
                             if (on) test_leaf<CAND, SHIFT>(a, c, out, j, q, f, rs2);
                         }
                     } else {
@@ -558,7 +627,7 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                             bool acc = false;
                             int id = 0;
                             if (jj <= l) {
-                                const float4 q = __ldg(a.leaves + jj);
+                                const float4 q = tree_ld(a.leaves + jj);
                                 acc = on && leaf_accepts<CAND, SHIFT>(a, c, jj, q, f, rs2);
                                 id = __float_as_int(q.w) & 0x7FFFFFFF;
                             }
@@ -574,7 +643,7 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
             }
         } else {
             const int j = ~node;
-            const float4 q = __ldg(a.leaves + j);
+            const float4 q = tree_ld(a.leaves + j);
             if (W == 1) {
                 if (on) test_leaf<CAND, SHIFT>(a, c, out, j, q, f, rs2);
             } else {
@@ -595,7 +664,21 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
 // W lanes per particle: a warp serves 32 / W consecutive Z-order particles;
 // lane l works for particle l % (32 / W) and takes every W-th leaf of a bundle
 // starting at l / (32 / W).
-template <bool WIDE, bool CAND, int FMT, int W>
+//
+// PHASE 2 (the default) walks every periodic image in one launch.  With
+// QBVH_QUERY_SPLIT_IMAGES = 1 the images go to two launches instead: PHASE 0
+// walks the zero image of every tree (a particle lies inside its own box, so
+// this image is never empty) and PHASE 1 the other images, which only
+// particles within the search radius of a box face need, appending after the
+// phase-0 entries (the count comes from counts[]).  The split removes the
+// register spills of the zero-image walk but the image launch runs with few
+// busy warps: 1.92 ms in one launch against 2.01 ms in two at N = 2M.
+// ONE: a single tree (one system, one type), segment and type loops
+// compiled out.
+#ifndef QBVH_QUERY_SPLIT_IMAGES
+#define QBVH_QUERY_SPLIT_IMAGES 0
+#endif
+template <bool WIDE, bool CAND, int FMT, int W, bool ONE, int PHASE>
 __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ QueryArgs a)
 {
     constexpr int G = 32 / W;
@@ -611,10 +694,10 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
         me = __ldg(a.leaves + s);
         i_orig = __float_as_int(me.w) & 0x7FFFFFFF;
         if (i_orig >= a.n) {
-            atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
+            if (PHASE == 0) atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
             i_orig = s;
         }
-        seg_i = seg_of_sorted<WIDE>(a, s);
+        seg_i = ONE ? 0 : seg_of_sorted<WIDE>(a, s);
     }
     Query c;
     c.xi = me.x;
@@ -624,15 +707,16 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
     Row out;
     out.row = a.rows + (size_t)i_orig * a.cap;
     out.cap = a.cap;
-    out.count = 0;
-    const int T = a.n_types;
+    out.count = (PHASE == 1 && active) ? a.counts[i_orig] : 0;
+    bool walked = PHASE != 1;
+    const int T = ONE ? 1 : a.n_types;
     // the warp's particles may belong to several trees (segment boundaries):
     // take one segment value at a time
     unsigned remaining = __ballot_sync(FULL, active);
     while (remaining) {
-        const int seg = __shfl_sync(FULL, seg_i, __ffs(remaining) - 1);
-        const bool part = active && seg_i == seg;
-        remaining &= ~__ballot_sync(FULL, part);
+        const int seg = ONE ? 0 : __shfl_sync(FULL, seg_i, __ffs(remaining) - 1);
+        const bool part = ONE ? active : (active && seg_i == seg);
+        remaining = ONE ? 0u : (remaining & ~__ballot_sync(FULL, part));
         const int sys = seg / T;
         const int ta = seg - sys * T;
         const float L = a.sys[sys].L;
@@ -644,27 +728,56 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
             c.rl2 = a.rl2[ta * T + tb];
             const float rs2 = a.rs2[ta * T + tb];
             const Frame f = frame_of(g);
-            const unsigned mine = part ? image_mask(me.x, me.y, me.z, L, g, rs2) : 0u;
-            unsigned mask = __reduce_or_sync(FULL, mine);
             const int root = g.count >= 2 ? g.start : ~g.start;
             const int last = g.start + g.count - 1;
+            if (PHASE == 0) {
+                // zero image: the walk's own root test decides whether it is empty
+                set_image(c, 13, L);
+                warp_walk<CAND, FMT, false, W>(a, c, out, g, f, root, last, part, rs2, wsub, same);
+                continue;
+            }
+            unsigned mine = part ? image_mask(me.x, me.y, me.z, L, g, rs2) : 0u;
+            if (PHASE == 1) mine &= ~(1u << 13);
+            unsigned mask = __reduce_or_sync(FULL, mine);
+            walked = walked || mask != 0u;
             while (mask) {
                 const int img = __ffs(mask) - 1;
                 mask &= mask - 1u;
                 set_image(c, img, L);
                 const bool on = (mine >> img) & 1u;
-                if (img == 13)
+                if (PHASE == 2 && img == 13)
                     warp_walk<CAND, FMT, false, W>(a, c, out, g, f, root, last, on, rs2, wsub, same);
                 else
                     warp_walk<CAND, FMT, true, W>(a, c, out, g, f, root, last, on, rs2, wsub, same);
             }
         }
     }
-    if (active && wsub == 0) a.counts[i_orig] = out.count;
+    if (!walked) return;   // phase 1, no image to add for this warp: counts stay
+    if (active && wsub == 0) {
+        // the row index again (not kept live across the walk)
+        int io = __float_as_int(__ldg(a.leaves + s).w) & 0x7FFFFFFF;
+        a.counts[io < a.n ? io : s] = out.count;
+    }
     warp_max_count(active ? out.count : 0, a.status);
 }
 
 }  // namespace
+
+template <int FMT, int W, int PHASE>
+static void launch_warp_phase(const QueryArgs &a, cudaStream_t s, int grid)
+{
+    const int b = a.block;
+    if (a.wide_keys) {
+        if (a.candidates) query_warp_kernel<true, true, FMT, W, false, PHASE><<<grid, b, 0, s>>>(a);
+        else query_warp_kernel<true, false, FMT, W, false, PHASE><<<grid, b, 0, s>>>(a);
+    } else if (a.candidates) {
+        query_warp_kernel<false, true, FMT, W, false, PHASE><<<grid, b, 0, s>>>(a);
+    } else if (a.n_types == 1) {
+        query_warp_kernel<false, false, FMT, W, true, PHASE><<<grid, b, 0, s>>>(a);
+    } else {
+        query_warp_kernel<false, false, FMT, W, false, PHASE><<<grid, b, 0, s>>>(a);
+    }
+}
 
 template <int FMT, int W>
 static void launch_warp(const QueryArgs &a, cudaStream_t s)
@@ -672,13 +785,12 @@ static void launch_warp(const QueryArgs &a, cudaStream_t s)
     const int b = a.block;
     const long long threads = (long long)((a.n + (32 / W) - 1) / (32 / W)) * 32;
     const int grid = (int)((threads + b - 1) / b);
-    if (a.wide_keys) {
-        if (a.candidates) query_warp_kernel<true, true, FMT, W><<<grid, b, 0, s>>>(a);
-        else query_warp_kernel<true, false, FMT, W><<<grid, b, 0, s>>>(a);
-    } else {
-        if (a.candidates) query_warp_kernel<false, true, FMT, W><<<grid, b, 0, s>>>(a);
-        else query_warp_kernel<false, false, FMT, W><<<grid, b, 0, s>>>(a);
-    }
+#if QBVH_QUERY_SPLIT_IMAGES
+    launch_warp_phase<FMT, W, 0>(a, s, grid);
+    launch_warp_phase<FMT, W, 1>(a, s, grid);
+#else
+    launch_warp_phase<FMT, W, 2>(a, s, grid);
+#endif
 }
 
 template <int FMT>
