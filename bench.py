@@ -109,9 +109,9 @@ PROFILED_TRAFFIC = {
     "entries": [],
 }
 # kernels of one timed step: build = prepare, Morton (+ sort histograms), segment
-# scan, 4 onesweep passes (30-bit keys, 8-bit digits), Karras, fit; query = 2
-# traversal launches (zero image, other images); LJ = forward + fixed-order FP64 finalize
-KERNELS_PER_STEP = 9 + 2 + 2
+# scan, 4 onesweep passes (30-bit keys, 8-bit digits), Karras, fit; query = 1
+# traversal launch (all periodic images); LJ = forward + fixed-order FP64 finalize
+KERNELS_PER_STEP = 9 + 1 + 2
 _TRAFFIC_SOURCES = ("paper_1901_08088_gb300/csrc/query.cu", "paper_1901_08088_gb300/csrc/qbvh_internal.cuh")
 
 
