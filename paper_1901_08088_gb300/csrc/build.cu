@@ -376,32 +376,58 @@ __device__ __forceinline__ int arrive_acq_rel(int *p)
     return old;
 }
 
+// Bottom-up fit, in two parts.
+//
+// Block part.  A block owns leaves [b0, b1] and the internal nodes with the
+// same indices.  An internal node whose leaf range lies inside [b0, b1] is
+// "local": its Karras index (an end of its range) is then in [b0, b1] too,
+// and so are its children.  Every thread loads the words of its own leaf and
+// node (coalesced), then the block settles its local nodes level by level:
+// in each round a node whose children are done is computed from the
+// children's boxes in shared memory; a barrier separates the rounds.
+//
+// Global part.  Nodes whose range crosses a block boundary are completed by
+// climbing: the thread of every local subtree root (and of every leaf whose
+// parent crosses) arrives at the parent through a device-scope
+// acquire-release counter; the second arrival computes the parent from its
+// children's words in global memory (every node and leaf is written there)
+// and climbs on.
 template <bool WIDE, bool F32>
-__global__ void __launch_bounds__(kBlock) fit_kernel(const BuildArgs a)
+__device__ __forceinline__ void fit_compute(const BuildArgs &a, int node, const int2 r, const int2 c, int rope,
+                                            uint2 bl, uint2 br, const float4 &lo_a, const float4 &hi_a,
+                                            const float4 &lo_b, const float4 &hi_b, uint2 *q_out, float4 *lo_out,
+                                            float4 *hi_out)
 {
-    const int k = blockIdx.x * kBlock + threadIdx.x;
-    if (k >= a.n) return;
-    const unsigned long long key = key_at<WIDE>(a.keys_sorted, k);
-    const int s = seg_of_key<WIDE>(key, a.n_types);
-    const SegInfo g = a.seg[s];
-    const int hi = g.start + g.count - 1;
-
-    int orig = __ldg(a.order + k);
-    if ((unsigned)orig >= (unsigned)a.n) {
-        atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
-        orig = 0;
+    const unsigned qlo = qmin3(bl.x, br.x);
+    const unsigned qhi = qmax3(bl.y, br.y);
+    const int count = r.y - r.x + 1;
+    const int bundle = (a.bundle_k >= 2 && count <= a.bundle_k) ? 1 : 0;
+    int4 w;
+    w.x = (int)(qlo | ((unsigned)bundle << 31));
+    w.y = (int)qhi;
+    w.z = bundle ? r.x : c.x;
+    w.w = rope;
+    __stcg(a.nodes + node, w);
+    if (q_out) *q_out = make_uint2(qlo, qhi);
+    if (F32) {
+        // exact FP32 AABB: min / max of the children's boxes (Fig. 3a layout)
+        const float4 lo = make_float4(fminf(lo_a.x, lo_b.x), fminf(lo_a.y, lo_b.y), fminf(lo_a.z, lo_b.z), 0.f);
+        const float4 hb = make_float4(fmaxf(hi_a.x, hi_b.x), fmaxf(hi_a.y, hi_b.y), fmaxf(hi_a.z, hi_b.z), 0.f);
+        if (lo_out) {
+            *lo_out = lo;
+            *hi_out = hb;
+        }
+        float lx = lo.x;
+        if (bundle) lx = __int_as_float(__float_as_int(lx) | 0x80000000);
+        __stcg(a.nodes32 + 2 * (size_t)node, make_float4(lx, lo.y, lo.z, __int_as_float(w.z)));
+        __stcg(a.nodes32 + 2 * (size_t)node + 1, make_float4(hb.x, hb.y, hb.z, __int_as_float(w.w)));
     }
-    const float4 p = __ldg(a.pos + orig);
-    const int rope = rope_after(a.range, k, hi);
-    const unsigned tag = (unsigned)orig | ((rope >= 0 ? 1u : 0u) << 31);
-    a.leaves[k] = make_float4(p.x, p.y, p.z, __uint_as_float(tag));
+}
 
-    uint2 q;
-    q.x = pack3(q_down(p.x, g.rlo[0], g.h[0]), q_down(p.y, g.rlo[1], g.h[1]), q_down(p.z, g.rlo[2], g.h[2]));
-    q.y = pack3(q_up(p.x, g.rlo[0], g.h[0]), q_up(p.y, g.rlo[1], g.h[1]), q_up(p.z, g.rlo[2], g.h[2]));
-    a.leaf_q[k] = q;
-
-    int node = a.par_leaf[k];
+// Climb from `node` while this thread is the second arrival (global part).
+template <bool WIDE, bool F32>
+__device__ __forceinline__ void fit_climb(const BuildArgs &a, int node, int hi)
+{
     // a radix tree over 62-bit keys (30-bit code + 32-bit position) is at most
     // 63 levels deep; a longer walk means a broken parent link
     for (int depth = 0; node >= 0; ++depth) {
@@ -409,15 +435,20 @@ __global__ void __launch_bounds__(kBlock) fit_kernel(const BuildArgs a)
             atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
             return;
         }
-        // arrive: release publishes this child's bounds, acquire makes the
-        // sibling's bounds visible to the thread that continues upward
-        if (arrive_acq_rel(a.visit + node) == 0) return;   // sibling not done yet
+        // the node's own words do not depend on the arrival: load them first
+        const int2 r = a.range[node];
         const int2 c = a.child[node];
+        const int up = a.par_int[node];
+        const int rope = rope_after(a.range, r.y, hi);
+        // release publishes this child's bounds, acquire makes the sibling's
+        // bounds visible to the thread that continues upward
+        if (arrive_acq_rel(a.visit + node) == 0) return;   // sibling not done yet
         if (c.x >= a.n || ~c.x >= a.n || c.y >= a.n || ~c.y >= a.n) {
             atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
             return;
         }
         uint2 bl, br;
+        float4 lo_a, hi_a, lo_b, hi_b;
         if (c.x >= 0) {
             int4 w = __ldcg(a.nodes + c.x);
             bl = make_uint2((unsigned)w.x & QBVH_QMASK, (unsigned)w.y);
@@ -430,20 +461,7 @@ __global__ void __launch_bounds__(kBlock) fit_kernel(const BuildArgs a)
         } else {
             br = __ldcg(a.leaf_q + ~c.y);
         }
-        const unsigned qlo = qmin3(bl.x, br.x);
-        const unsigned qhi = qmax3(bl.y, br.y);
-        const int2 r = a.range[node];
-        const int count = r.y - r.x + 1;
-        const int bundle = (a.bundle_k >= 2 && count <= a.bundle_k) ? 1 : 0;
-        int4 w;
-        w.x = (int)(qlo | ((unsigned)bundle << 31));
-        w.y = (int)qhi;
-        w.z = bundle ? r.x : c.x;
-        w.w = rope_after(a.range, r.y, hi);
-        __stcg(a.nodes + node, w);
         if (F32) {
-            // exact FP32 AABB: min / max of the children's boxes (Fig. 3a layout)
-            float4 lo_a, hi_a, lo_b, hi_b;
             if (c.x >= 0) {
                 lo_a = __ldcg(a.nodes32 + 2 * (size_t)c.x);
                 hi_a = __ldcg(a.nodes32 + 2 * (size_t)c.x + 1);
@@ -458,15 +476,113 @@ __global__ void __launch_bounds__(kBlock) fit_kernel(const BuildArgs a)
             } else {
                 lo_b = hi_b = __ldcg(a.leaves + ~c.y);
             }
-            float lx = fminf(lo_a.x, lo_b.x);
-            if (bundle) lx = __int_as_float(__float_as_int(lx) | 0x80000000);
-            __stcg(a.nodes32 + 2 * (size_t)node,
-                   make_float4(lx, fminf(lo_a.y, lo_b.y), fminf(lo_a.z, lo_b.z), __int_as_float(w.z)));
-            __stcg(a.nodes32 + 2 * (size_t)node + 1,
-                   make_float4(fmaxf(hi_a.x, hi_b.x), fmaxf(hi_a.y, hi_b.y), fmaxf(hi_a.z, hi_b.z),
-                               __int_as_float(w.w)));
         }
-        node = a.par_int[node];
+        fit_compute<WIDE, F32>(a, node, r, c, rope, bl, br, lo_a, hi_a, lo_b, hi_b, nullptr, nullptr, nullptr);
+        node = up;
+    }
+}
+
+template <bool WIDE, bool F32>
+__global__ void __launch_bounds__(kBlock) fit_kernel(const BuildArgs a)
+{
+    __shared__ int s_done[kBlock];                  // local internal node b0 + t settled
+    __shared__ uint2 s_q[kBlock];                   // quantized box of internal node b0 + t
+    __shared__ uint2 s_lq[kBlock];                  // quantized box of leaf b0 + t
+    __shared__ float4 s_lo[F32 ? kBlock : 1];       // FP32 box of internal node b0 + t
+    __shared__ float4 s_hi[F32 ? kBlock : 1];
+    __shared__ float4 s_leaf[F32 ? kBlock : 1];     // FP32 position of leaf b0 + t
+    const int t = threadIdx.x;
+    const int b0 = blockIdx.x * kBlock;
+    const int b1 = min(b0 + kBlock, a.n) - 1;
+    const int k = b0 + t;
+    const bool live = k < a.n;
+    s_done[t] = 0;
+
+    // ---- leaf k and the words of internal node k --------------------------
+    int hi = 0, leaf_up = -1;
+    bool node_valid = false;
+    int2 r = make_int2(0, -1), c = make_int2(0, 0);
+    int up = -1, rope = QBVH_END;
+    if (live) {
+        const unsigned long long key = key_at<WIDE>(a.keys_sorted, k);
+        const int sg = seg_of_key<WIDE>(key, a.n_types);
+        const SegInfo g = a.seg[sg];
+        hi = g.start + g.count - 1;
+        int orig = __ldg(a.order + k);
+        if ((unsigned)orig >= (unsigned)a.n) {
+            atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
+            orig = 0;
+        }
+        const float4 p = __ldg(a.pos + orig);
+        const int leaf_rope = rope_after(a.range, k, hi);
+        const unsigned tag = (unsigned)orig | ((leaf_rope >= 0 ? 1u : 0u) << 31);
+        const float4 leaf = make_float4(p.x, p.y, p.z, __uint_as_float(tag));
+        a.leaves[k] = leaf;
+        uint2 q;
+        q.x = pack3(q_down(p.x, g.rlo[0], g.h[0]), q_down(p.y, g.rlo[1], g.h[1]), q_down(p.z, g.rlo[2], g.h[2]));
+        q.y = pack3(q_up(p.x, g.rlo[0], g.h[0]), q_up(p.y, g.rlo[1], g.h[1]), q_up(p.z, g.rlo[2], g.h[2]));
+        a.leaf_q[k] = q;
+        s_lq[t] = q;
+        if (F32) s_leaf[t] = leaf;
+        leaf_up = a.par_leaf[k];
+        // internal node k exists for every leaf index of a tree but its last
+        node_valid = k <= hi - 1;
+        if (node_valid) {
+            r = a.range[k];
+            c = a.child[k];
+            up = a.par_int[k];
+            rope = rope_after(a.range, r.y, hi);
+        }
+    }
+    const bool local = node_valid && r.x >= b0 && r.y <= b1;
+    if (local && (k < r.x || k > r.y)) atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
+    bool pending = local && k >= r.x && k <= r.y;
+    __syncthreads();
+
+    // ---- block part: rounds over the local nodes -----------------------------
+    for (int round = 0; round < kBlock; ++round) {
+        bool done_now = false;
+        if (pending) {
+            const int ia = (c.x >= 0 ? c.x : ~c.x) - b0, ib = (c.y >= 0 ? c.y : ~c.y) - b0;
+            if ((unsigned)ia >= (unsigned)kBlock || (unsigned)ib >= (unsigned)kBlock) {
+                atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
+                pending = false;
+            } else if ((c.x < 0 || s_done[ia]) && (c.y < 0 || s_done[ib])) {
+                const uint2 bl = c.x >= 0 ? s_q[ia] : s_lq[ia];
+                const uint2 br = c.y >= 0 ? s_q[ib] : s_lq[ib];
+                float4 lo_a, hi_a, lo_b, hi_b;
+                if (F32) {
+                    lo_a = c.x >= 0 ? s_lo[ia] : s_leaf[ia];
+                    hi_a = c.x >= 0 ? s_hi[ia] : s_leaf[ia];
+                    lo_b = c.y >= 0 ? s_lo[ib] : s_leaf[ib];
+                    hi_b = c.y >= 0 ? s_hi[ib] : s_leaf[ib];
+                }
+                fit_compute<WIDE, F32>(a, k, r, c, rope, bl, br, lo_a, hi_a, lo_b, hi_b, &s_q[t],
+                                       F32 ? &s_lo[t] : nullptr, F32 ? &s_hi[t] : nullptr);
+                done_now = true;
+                pending = false;
+            }
+        }
+        __syncthreads();                 // this round's boxes are written
+        if (done_now) s_done[t] = 1;
+        if (!__syncthreads_or(pending)) break;   // and its flags visible
+    }
+    if (pending) atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);   // a cycle: broken links
+
+    // ---- global part: climb from the roots of the local subtrees -------------
+    // (a leaf or local node whose parent is not local; the parent's range
+    // decides, and a parent's range contains its child's)
+    if (live && leaf_up >= 0 && leaf_up < a.n) {
+        const int2 pr = a.range[leaf_up];
+        if (!(pr.x >= b0 && pr.y <= b1)) fit_climb<WIDE, F32>(a, leaf_up, hi);
+    } else if (live && leaf_up >= a.n) {
+        atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
+    }
+    if (local && up >= 0 && up < a.n) {
+        const int2 pr = a.range[up];
+        if (!(pr.x >= b0 && pr.y <= b1)) fit_climb<WIDE, F32>(a, up, hi);
+    } else if (local && up >= a.n) {
+        atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
     }
 }
 
