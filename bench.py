@@ -105,8 +105,13 @@ class ClockSampler:
 # the traversal sources whose SHA-256 prefix is given; any other source or options
 # report null.
 PROFILED_TRAFFIC = {
-    "source_sha256": "",
-    "entries": [],
+    "source_sha256": "5b06f29dce555c48",
+    "entries": [
+        {"options": {"bundle_k": 16, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
+         "bytes": 459.93e6 + 1.33e9},
+        {"options": {"bundle_k": 32, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
+         "bytes": 422.97e6 + 1.32e9},
+    ],
 }
 # kernels of one timed step: build = prepare, Morton (+ sort histograms), segment
 # scan, 4 onesweep passes (30-bit keys, 8-bit digits), Karras, fit; query = 1
