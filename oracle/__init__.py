@@ -15,6 +15,9 @@ Contents (C sources compiled with gcc into ``_oracle.so``):
   outward quantization with IEEE directed rounding (Sec. 3).
 * ``lj_ref.c``    -- FP64 truncated-shifted Lennard-Jones energy (Eq. 1),
   forces and per-type-pair parameter gradients.
+* ``nlist64_ref.c`` -- neighbor lists of double-precision particle data
+  (Sec. 2.2): brute force and 27-cell list with one pinned FP64 decision
+  expression.
 
 Pins: every function here is checked by ``tests/test_oracle_*.py`` against
 closed forms, brute force, golden hand-derived fixtures and invariants.
@@ -30,7 +33,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_oracle.so")
-_SRCS = ["nlist_ref.c", "lbvh_ref.c", "lj_ref.c"]
+_SRCS = ["nlist_ref.c", "lbvh_ref.c", "lj_ref.c", "nlist64_ref.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -68,6 +71,10 @@ def lib():
             L.or_nlist_cell.restype = i32
             L.or_band_check.argtypes = [i32, P, P, f32, i32, P, f64, i32, P, P, i32, P, i32, P]
             L.or_band_check.restype = C.c_long
+            L.or_nlist64_brute.argtypes = [i32, P, P, f64, i32, P, i32, P, P]
+            L.or_nlist64_brute.restype = i32
+            L.or_nlist64_cell.argtypes = [i32, P, P, f64, i32, P, i32, P, P]
+            L.or_nlist64_cell.restype = i32
             L.or_num_threads.argtypes = []
             L.or_num_threads.restype = i32
             L.or_morton.argtypes = [i32, P, P, P, P]
@@ -119,6 +126,22 @@ def nlist(pos, L, r_list, types=None, n_types=1, cap=256, method="cell"):
     rc = fn(n, _p(pos), _p(types), float(np.float32(L)), n_types, _p(rl), cap, _p(rows), _p(counts))
     if rc != 0:
         raise RuntimeError(f"oracle nlist failed ({rc})")
+    return rows, counts
+
+
+def nlist64(pos, L, r_list, types=None, n_types=1, cap=256, method="cell"):
+    """Exact neighbor list of FP64 positions (FP64 decision, FP32 list radii).
+    Returns (rows [n,cap] int32 sorted asc, counts [n] int32)."""
+    pos = _c(pos, np.float64).reshape(-1, 3)
+    n = pos.shape[0]
+    types = np.zeros(n, np.int32) if types is None else _c(types, np.int32)
+    rl = _rl_matrix(r_list, n_types)
+    rows = np.full((n, cap), -1, np.int32)
+    counts = np.zeros(n, np.int32)
+    fn = lib().or_nlist64_brute if method == "brute" else lib().or_nlist64_cell
+    rc = fn(n, _p(pos), _p(types), float(L), n_types, _p(rl), cap, _p(rows), _p(counts))
+    if rc != 0:
+        raise RuntimeError(f"oracle nlist64 failed ({rc})")
     return rows, counts
 
 

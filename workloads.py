@@ -16,6 +16,8 @@ not published, so seeded stand-ins with the same shapes are generated here:
 * ``batched_ensemble``  -- many independent jittered-lattice systems of
   uneven N and density.
 * ``two_type_lj``       -- jittered lattice with a 50/50 random type split.
+* ``jittered_lattice64`` -- the jittered lattice kept in double precision
+  (the paper's double-precision particle data, Sec. 2.2, Sec. 4.1-4.2).
 
 Conventions (all generators):
 * FP64 arithmetic, rounded to float32 once at the end.
@@ -35,6 +37,10 @@ import numpy as np
 
 __all__ = [
     "System",
+    "System64",
+    "jittered_lattice64",
+    "pack_double4",
+    "WCA_RCUT",
     "box_edge",
     "jittered_lattice",
     "binary_mixture",
@@ -70,6 +76,34 @@ class System:
         return int(self.pos.shape[0])
 
 
+@dataclass
+class System64:
+    """One periodic configuration with double-precision particle data.
+
+    pos   : float64 [N, 3], every coordinate in [0, L)
+    types : int32 [N], values in [0, n_types)
+    L     : float (FP64) cubic box edge, authoritative
+    r_list: float32 [n_types, n_types] list radius (r_cut + skin)
+    r_cut : float32 [n_types, n_types]
+    """
+
+    pos: np.ndarray
+    types: np.ndarray
+    L: float
+    n_types: int
+    r_list: np.ndarray
+    r_cut: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.pos.shape[0])
+
+
+# WCA cutoff: LJ truncated at its minimum, r_c = 2^(1/6) sigma (Sec. 4.2)
+WCA_RCUT = float(2.0 ** (1.0 / 6.0))
+
+
 def _rng(seed) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(seed))
 
@@ -96,17 +130,8 @@ def _matrix(n_types: int, value) -> np.ndarray:
     return np.ascontiguousarray(m.astype(np.float32))
 
 
-def jittered_lattice(n: int, rho: float, jitter: float, seed,
-                     r_cut: float = 3.0, skin: float = 0.3) -> System:
-    """Simple-cubic lattice with per-axis uniform jitter in [-jitter, +jitter].
-
-    m = ceil(N^(1/3)) sites per axis with spacing a = L / m; when m^3 > N a
-    seeded permutation picks which N sites are occupied.
-    """
-    if n <= 0:
-        raise ValueError("n must be positive")
-    rng = _rng(seed)
-    L = box_edge(n, rho)
+def _lattice_f64(n: int, L: float, jitter: float, rng):
+    """FP64 jittered simple-cubic sites (unwrapped) and the sites per axis."""
     m = int(round(n ** (1.0 / 3.0)))
     if m ** 3 < n:
         m += 1
@@ -122,12 +147,47 @@ def jittered_lattice(n: int, rho: float, jitter: float, seed,
     iz = sites % m
     base = (np.stack([ix, iy, iz], axis=1).astype(np.float64) + 0.5) * a
     jit = rng.uniform(-jitter, jitter, size=(n, 3))
-    pos = _wrap_to_f32(base + jit, L)
+    return base + jit, m, a
+
+
+def jittered_lattice(n: int, rho: float, jitter: float, seed,
+                     r_cut: float = 3.0, skin: float = 0.3) -> System:
+    """Simple-cubic lattice with per-axis uniform jitter in [-jitter, +jitter].
+
+    m = ceil(N^(1/3)) sites per axis with spacing a = L / m; when m^3 > N a
+    seeded permutation picks which N sites are occupied.
+    """
+    if n <= 0:
+        raise ValueError("n must be positive")
+    rng = _rng(seed)
+    L = box_edge(n, rho)
+    x64, m, a = _lattice_f64(n, float(L), jitter, rng)
+    pos = _wrap_to_f32(x64, L)
     rl = np.float32(r_cut) + np.float32(skin)
     return System(pos=np.ascontiguousarray(pos), types=np.zeros(n, np.int32), L=L,
                   n_types=1, r_list=_matrix(1, rl), r_cut=_matrix(1, r_cut),
                   meta=dict(kind="jittered_lattice", n=n, rho=rho, jitter=jitter,
                             seed=seed, sites_per_axis=m, spacing=a))
+
+
+def jittered_lattice64(n: int, rho: float, jitter: float, seed,
+                       r_cut: float = 3.0, skin: float = 0.3) -> System64:
+    """The jittered lattice in double precision: L = (N / rho)^(1/3) in FP64
+    (not rounded to FP32), positions wrapped into [0, L) in FP64.  The list
+    radius is the FP32 value of r_cut + skin."""
+    if n <= 0:
+        raise ValueError("n must be positive")
+    rng = _rng(seed)
+    L = float((n / rho) ** (1.0 / 3.0))
+    x64, m, a = _lattice_f64(n, L, jitter, rng)
+    pos = np.mod(x64, L)
+    pos[pos >= L] = 0.0
+    pos[pos < 0] = 0.0
+    rl = np.float32(np.float32(r_cut) + np.float32(skin))
+    return System64(pos=np.ascontiguousarray(pos), types=np.zeros(n, np.int32), L=L,
+                    n_types=1, r_list=_matrix(1, rl), r_cut=_matrix(1, r_cut),
+                    meta=dict(kind="jittered_lattice64", n=n, rho=rho, jitter=jitter,
+                              seed=seed, sites_per_axis=m, spacing=a))
 
 
 def _periodic_d2(a: np.ndarray, b: np.ndarray, L: float) -> np.ndarray:
@@ -256,6 +316,15 @@ def pack_float4(pos: np.ndarray, types: np.ndarray) -> np.ndarray:
     out = np.zeros((n, 4), np.float32)
     out[:, :3] = pos
     out.view(np.int32)[:, 3] = types.astype(np.int32)
+    return out
+
+
+def pack_double4(pos: np.ndarray, types: np.ndarray) -> np.ndarray:
+    """[N,3] float64 + [N] int32 -> [N,4] float64 with w holding the type as a whole number."""
+    n = pos.shape[0]
+    out = np.zeros((n, 4), np.float64)
+    out[:, :3] = pos
+    out[:, 3] = types.astype(np.float64)
     return out
 
 
