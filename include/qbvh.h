@@ -152,6 +152,31 @@ int qbvh_build(qbvh_handle h, const void *pos_dev, int n, float L, int n_types,
                cudaStream_t stream);
 
 /*
+ * Build the LBVH of one periodic system whose particle data is in double
+ * precision (Sec. 2.2: the boxes need not be; every FP32 or quantized box
+ * must enclose the exact particle, so a coordinate x enters the tree as the
+ * FP32 box [round-down(x), round-up(x)]).  The list the next qbvh_query
+ * writes is exact for the FP64 positions: j is a neighbor of i when the FP64
+ * minimum-image expression
+ *     dx = xj - xi;  dx = dx - L * rint(dx * (1/L))   (y, z alike)
+ *     d2 = (dx*dx + dy*dy) + dz*dz  <  (double)r_list * (double)r_list
+ * holds in IEEE double arithmetic without contraction.  The traversal runs
+ * in FP32 with the padded search sphere of Sec. 2.3; the leaf test takes
+ * FP32 positions rounded to nearest and defers to the FP64 positions only
+ * for the pairs within a proven error band of r_list (qbvh_query).
+ *
+ * pos64_dev : [n] double4 {x, y, z, w}, 32-byte aligned, x,y,z in [0, L),
+ *             w = the particle's type as a whole number in [0, n_types).
+ * L         : cubic box edge in FP64, finite and > 0 (its nearest FP32
+ *             value is used for the FP32 parts).
+ * n_types   : 1..4.
+ * The uniform-grid method and the candidate mode do not take FP64 data
+ * (QBVH_ERR_INVALID_ARG).  Errors and device-side validation as qbvh_build.
+ */
+int qbvh_build_f64(qbvh_handle h, const void *pos64_dev, int n, double L, int n_types,
+                   cudaStream_t stream);
+
+/*
  * Build the trees of n_sys independent periodic systems in one launch
  * sequence (one tree per system and type).  System k owns particles
  * [sys_offsets_host[k], sys_offsets_host[k+1]) of pos_dev and the cubic box

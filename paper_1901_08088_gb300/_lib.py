@@ -42,6 +42,7 @@ _lib = None
 P = C.c_void_p
 I = C.c_int
 F = C.c_float
+D = C.c_double
 PP = C.POINTER(C.c_void_p)
 PI = C.POINTER(C.c_int)
 
@@ -53,6 +54,7 @@ SIGNATURES = {
     "qbvh_set_option": (I, [P, I, I]),
     "qbvh_get_option": (I, [P, I, PI]),
     "qbvh_build": (I, [P, P, I, F, I, P]),
+    "qbvh_build_f64": (I, [P, P, I, D, I, P]),
     "qbvh_build_batched": (I, [P, P, I, I, P, P, I, P]),
     "qbvh_query": (I, [P, P, I, I, P]),
     "qbvh_query_async": (I, [P, P, I, P]),

@@ -67,6 +67,8 @@ struct qbvh_ctx {
     std::vector<float> L;
     std::vector<SysInfo> sysinfo;
     float L_min = 0.f, L_max = 0.f;
+    bool f64 = false;        // last build was of double-precision particle data
+    double L64 = 0.0;        // its FP64 box edge
     // last query
     bool have_list = false;
     int cap = 0;
@@ -77,6 +79,7 @@ struct qbvh_ctx {
     DevBuf seg, acc, seg_start, frames, sys, sys_off, status;
     DevBuf rows, counts;
     DevBuf cell_start, stype;
+    DevBuf leaves64;
     DevBuf lj_partials, lj_blk_sys, lj_blk_first, lj_sys_blk;
     std::vector<int> lj_layout_off;   // offsets the LJ block tables were built for
     int lj_n_blocks = 0;
@@ -170,13 +173,24 @@ int map_dev_err(unsigned err)
     return QBVH_OK;
 }
 
+// pos64_dev != nullptr: double-precision particle data of one system
+// (double4 {x, y, z, type}, 32-byte aligned) with FP64 box edge L64; L[0] is
+// then its nearest FP32 value.
 int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *off, const float *L, int n_types,
-               cudaStream_t s)
+               cudaStream_t s, const void *pos64_dev = nullptr, double L64 = 0.0)
 {
     if (!h) return QBVH_ERR_INVALID_ARG;
     if (n < 0 || n >= (1 << 30) || n_sys < 1 || n_sys > 65536) return QBVH_ERR_INVALID_ARG;
     if (n_types < 1 || n_types > QBVH_MAX_TYPES || n_sys * n_types > 65536) return QBVH_ERR_INVALID_ARG;
-    if (n > 0 && (!pos_dev || ((uintptr_t)pos_dev & 15u))) return QBVH_ERR_INVALID_ARG;
+    const bool f64 = pos64_dev != nullptr || L64 != 0.0;
+    if (f64) {
+        // one system, narrow keys (at most 4 types), the BVH method
+        if (n_sys != 1 || n_types > 4 || h->method != 0) return QBVH_ERR_INVALID_ARG;
+        if (n > 0 && (!pos64_dev || ((uintptr_t)pos64_dev & 31u))) return QBVH_ERR_INVALID_ARG;
+        if (!(L64 > 0.0) || !isfinite(L64)) return QBVH_ERR_INVALID_ARG;
+    } else if (n > 0 && (!pos_dev || ((uintptr_t)pos_dev & 15u))) {
+        return QBVH_ERR_INVALID_ARG;
+    }
     if (!off || !L) return QBVH_ERR_INVALID_ARG;
     if (off[0] != 0 || off[n_sys] != n) return QBVH_ERR_INVALID_ARG;
     for (int k = 0; k < n_sys; ++k) {
@@ -186,6 +200,8 @@ int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *of
     DeviceGuard g(h->device);
     h->built = false;
     h->have_list = false;
+    h->f64 = f64;
+    h->L64 = f64 ? L64 : 0.0;
     h->n = n;
     h->n_sys = n_sys;
     h->n_types = n_types;
@@ -235,6 +251,7 @@ int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *of
     rc = rc ? rc : ensure(h, h->nodes, nn * sizeof(int4));
     if (h->node_fmt == 1) rc = rc ? rc : ensure(h, h->nodes32, nn * 2 * sizeof(float4));
     rc = rc ? rc : ensure(h, h->leaves, nn * sizeof(float4));
+    if (f64) rc = rc ? rc : ensure(h, h->leaves64, nn * 4 * sizeof(double));
     rc = rc ? rc : ensure(h, h->leaf_q, nn * sizeof(uint2));
     rc = rc ? rc : ensure(h, h->range, nn * sizeof(int2));
     rc = rc ? rc : ensure(h, h->child, nn * sizeof(int2));
@@ -255,6 +272,9 @@ int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *of
     BuildArgs a;
     memset(&a, 0, sizeof a);
     a.pos = reinterpret_cast<const float4 *>(pos_dev);
+    a.pos64 = f64 ? reinterpret_cast<const double4_32a *>(pos64_dev) : nullptr;
+    a.L64 = L64;
+    a.leaves64 = f64 ? reinterpret_cast<double4_32a *>(h->leaves64.p) : nullptr;
     a.n = n;
     a.n_sys = n_sys;
     a.n_types = n_types;
@@ -369,14 +389,32 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
     if ((long long)h->n * cap >= (1LL << 40)) return QBVH_ERR_INVALID_ARG;
     QueryArgs q;
     memset(&q, 0, sizeof q);
+    if (h->f64 && h->candidates) return QBVH_ERR_INVALID_ARG;   // exact lists only for FP64 data
+    const double L_half = h->f64 ? h->L64 : (double)h->L_min;
     for (int a = 0; a < T; ++a)
         for (int b = 0; b < T; ++b) {
             const float r = r_list_host[a * T + b];
             if (!(r >= 0.f) || !isfinite(r) || r != r_list_host[b * T + a]) return QBVH_ERR_INVALID_ARG;
             // below half the box by a relative 2^-20: then a pair is found under
             // exactly one periodic image, the one the exact test selects
-            if (h->n > 0 && r > 0.f && !((double)r < 0.5 * (double)h->L_min * (1.0 - ldexp(1.0, -20))))
+            if (h->n > 0 && r > 0.f && !((double)r < 0.5 * L_half * (1.0 - ldexp(1.0, -20))))
                 return QBVH_ERR_CUTOFF_TOO_LARGE;
+            if (h->f64) {
+                // FP32 test of the rounded positions vs the FP64 decision: each
+                // component differs by at most eps = 2^-21 L for pairs within
+                // the radius (rounding of both positions and of L, 2^-24 L
+                // each, and of the two FP32 subtractions), so
+                // |d2_32 - d2_64| <= 2 sqrt(3) r eps + 3 eps^2 + 3 * 2^-24 (r + eps)^2
+                // < M below; outside [r^2 - M, r^2 + M] the FP32 test decides
+                const double r64 = (double)r, eps = ldexp(h->L64, -21);
+                const double r2 = r64 * r64;
+                const double M = 8.0 * r64 * eps + 4.0 * eps * eps + ldexp((r64 + eps) * (r64 + eps), -20);
+                float lo = (float)(r2 - M);
+                if ((double)lo > r2 - M) lo = nextafterf(lo, -INFINITY);
+                q.rl2_lo[a * T + b] = lo;
+                q.rl2_hi[a * T + b] = round_up_f(r2 + M);
+                q.r2_64[a * T + b] = r2;
+            }
             q.r_list[a * T + b] = r;
             q.rl2[a * T + b] = r * r;
             // padded search radius: covers FP32 rounding of the image position
@@ -422,6 +460,9 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
     q.traversal = h->traversal;
     q.warp_particles = h->warp_particles;
     q.block = h->query_block;
+    q.f64 = h->f64 ? 1 : 0;
+    q.leaves64 = h->f64 ? reinterpret_cast<const double4_32a *>(h->leaves64.p) : nullptr;
+    q.L64 = h->L64;
     launch_query(q, s);
     if (cudaMemcpyAsync(h->h_status, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return QBVH_ERR_CUDA;
@@ -499,7 +540,7 @@ int qbvh_destroy(qbvh_handle h)
                          &h->leaves, &h->leaf_q, &h->range, &h->child, &h->par_int, &h->par_leaf, &h->visit,
                          &h->seg, &h->acc, &h->seg_start, &h->frames, &h->sys, &h->sys_off, &h->status,
                          &h->rows, &h->counts, &h->cell_start, &h->stype, &h->lj_partials, &h->lj_blk_sys, &h->lj_blk_first,
-                         &h->lj_sys_blk};
+                         &h->lj_sys_blk, &h->leaves64};
         for (DevBuf *b : all) release(*b);
         if (h->h_status) cudaFreeHost(h->h_status);
     }
@@ -577,6 +618,15 @@ int qbvh_build(qbvh_handle h, const void *pos_dev, int n, float L, int n_types, 
 {
     int off[2] = {0, n};
     return build_impl(h, pos_dev, n, 1, off, &L, n_types, stream);
+}
+
+int qbvh_build_f64(qbvh_handle h, const void *pos64_dev, int n, double L, int n_types, cudaStream_t stream)
+{
+    if (!h || !(L > 0.0) || !isfinite(L)) return QBVH_ERR_INVALID_ARG;
+    const float L32 = (float)L;
+    if (!(L32 > 0.f) || !isfinite(L32)) return QBVH_ERR_INVALID_ARG;
+    int off[2] = {0, n};
+    return build_impl(h, nullptr, n, 1, off, &L32, n_types, stream, pos64_dev, L);
 }
 
 int qbvh_build_batched(qbvh_handle h, const void *pos_dev, int n_total, int n_sys, const int *sys_offsets_host,

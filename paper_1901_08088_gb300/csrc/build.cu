@@ -78,7 +78,24 @@ __global__ void prepare_kernel(unsigned *acc, int n_seg, DevStatus *status, unsi
     }
 }
 
-template <bool WIDE>
+// Double-precision particle data (Sec. 2.2): a coordinate x is bounded by
+// the FP32 box [rd(x), ru(x)], rounded down and up, so every FP32 or
+// quantized box built over it encloses the exact point.  NaN and negative
+// coordinates are read as 0 (the morton pass has flagged the build).
+__device__ __forceinline__ void read_pos64(const BuildArgs &a, int idx, float3 &lo, float3 &hi, float3 &mid,
+                                           double3 &xyz)
+{
+    const double4_32a q = a.pos64[idx];
+    const double x = (q.x >= 0.0) ? q.x : 0.0;
+    const double y = (q.y >= 0.0) ? q.y : 0.0;
+    const double z = (q.z >= 0.0) ? q.z : 0.0;
+    lo = make_float3(__double2float_rd(x), __double2float_rd(y), __double2float_rd(z));
+    hi = make_float3(__double2float_ru(x), __double2float_ru(y), __double2float_ru(z));
+    mid = make_float3(__double2float_rn(x), __double2float_rn(y), __double2float_rn(z));
+    xyz = make_double3(x, y, z);
+}
+
+template <bool WIDE, bool F64>
 __global__ void __launch_bounds__(kBlock) morton_kernel(const BuildArgs a, unsigned *acc)
 {
     __shared__ unsigned s_acc[kLocalSegs * 8];
@@ -109,26 +126,43 @@ __global__ void __launch_bounds__(kBlock) morton_kernel(const BuildArgs a, unsig
 
     unsigned err = 0u;
     int seg = -1;
-    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);   // lower corner of the particle's box
+    float3 ph = make_float3(0.f, 0.f, 0.f);        // upper corner
     if (i < a.n) {
         const int k = a.n_sys > 1 ? sys_of(a.sys_off, a.n_sys, i) : 0;
         const SysInfo sy = a.sys[k];
-        p = __ldg(a.pos + i);
-        int type = __float_as_int(p.w);
-        if (type < 0 || type >= T) {
-            err |= QBVH_DEVERR_BAD_TYPE;
-            type = type < 0 ? 0 : T - 1;
-        }
-        if (!(p.x >= 0.f && p.x < sy.L && p.y >= 0.f && p.y < sy.L && p.z >= 0.f && p.z < sy.L)) {
-            err |= QBVH_DEVERR_OUT_OF_BOX;
-            // keep the accumulators in the non-negative range; the build is
-            // reported as failed at the next query
-            p.x = fmaxf(p.x, 0.f);
-            p.y = fmaxf(p.y, 0.f);
-            p.z = fmaxf(p.z, 0.f);
-            if (!(p.x == p.x)) p.x = 0.f;
-            if (!(p.y == p.y)) p.y = 0.f;
-            if (!(p.z == p.z)) p.z = 0.f;
+        int type;
+        if (F64) {
+            const double4_32a q = a.pos64[i];
+            const bool type_ok = q.w >= 0.0 && q.w < (double)T && (double)(int)q.w == q.w;
+            if (!type_ok) err |= QBVH_DEVERR_BAD_TYPE;
+            if (!(q.x >= 0.0 && q.x < a.L64 && q.y >= 0.0 && q.y < a.L64 && q.z >= 0.0 && q.z < a.L64))
+                err |= QBVH_DEVERR_OUT_OF_BOX;
+            type = type_ok ? (int)q.w : 0;
+            float3 lo, hi, mid;
+            double3 xyz;
+            read_pos64(a, i, lo, hi, mid, xyz);
+            p = make_float4(lo.x, lo.y, lo.z, 0.f);
+            ph = hi;
+        } else {
+            p = __ldg(a.pos + i);
+            type = __float_as_int(p.w);
+            if (type < 0 || type >= T) {
+                err |= QBVH_DEVERR_BAD_TYPE;
+                type = type < 0 ? 0 : T - 1;
+            }
+            if (!(p.x >= 0.f && p.x < sy.L && p.y >= 0.f && p.y < sy.L && p.z >= 0.f && p.z < sy.L)) {
+                err |= QBVH_DEVERR_OUT_OF_BOX;
+                // keep the accumulators in the non-negative range; the build is
+                // reported as failed at the next query
+                p.x = fmaxf(p.x, 0.f);
+                p.y = fmaxf(p.y, 0.f);
+                p.z = fmaxf(p.z, 0.f);
+                if (!(p.x == p.x)) p.x = 0.f;
+                if (!(p.y == p.y)) p.y = 0.f;
+                if (!(p.z == p.z)) p.z = 0.f;
+            }
+            ph = make_float3(p.x, p.y, p.z);
         }
         const unsigned code = (spread10(bin_of(p.x, sy.mscale)) << 2) |
                               (spread10(bin_of(p.y, sy.mscale)) << 1) |
@@ -155,9 +189,9 @@ __global__ void __launch_bounds__(kBlock) morton_kernel(const BuildArgs a, unsig
     v[1] = __float_as_uint(p.x);
     v[2] = __float_as_uint(p.y);
     v[3] = __float_as_uint(p.z);
-    v[4] = v[1];
-    v[5] = v[2];
-    v[6] = v[3];
+    v[4] = __float_as_uint(ph.x);
+    v[5] = __float_as_uint(ph.y);
+    v[6] = __float_as_uint(ph.z);
     unsigned *dst_base = nullptr;
     if (uniform) {
         v[0] = __reduce_add_sync(full, 1u);
@@ -424,8 +458,23 @@ __device__ __forceinline__ void fit_compute(const BuildArgs &a, int node, const 
     }
 }
 
+// FP32 box of leaf k as written in global memory: the point itself, or for
+// double-precision data the outward-rounded box of the FP64 point.
+template <bool F64>
+__device__ __forceinline__ void leaf_box(const BuildArgs &a, int k, float4 &lo, float4 &hi)
+{
+    if (F64) {
+        const double2 *d2 = reinterpret_cast<const double2 *>(a.leaves64 + k);
+        const double2 xy = __ldcg(d2), zw = __ldcg(d2 + 1);
+        lo = make_float4(__double2float_rd(xy.x), __double2float_rd(xy.y), __double2float_rd(zw.x), 0.f);
+        hi = make_float4(__double2float_ru(xy.x), __double2float_ru(xy.y), __double2float_ru(zw.x), 0.f);
+    } else {
+        lo = hi = __ldcg(a.leaves + k);
+    }
+}
+
 // Climb from `node` while this thread is the second arrival (global part).
-template <bool WIDE, bool F32>
+template <bool WIDE, bool F32, bool F64>
 __device__ __forceinline__ void fit_climb(const BuildArgs &a, int node, int hi)
 {
     // a radix tree over 62-bit keys (30-bit code + 32-bit position) is at most
@@ -467,14 +516,14 @@ __device__ __forceinline__ void fit_climb(const BuildArgs &a, int node, int hi)
                 hi_a = __ldcg(a.nodes32 + 2 * (size_t)c.x + 1);
                 lo_a.x = clear_sign(lo_a.x);
             } else {
-                lo_a = hi_a = __ldcg(a.leaves + ~c.x);
+                leaf_box<F64>(a, ~c.x, lo_a, hi_a);
             }
             if (c.y >= 0) {
                 lo_b = __ldcg(a.nodes32 + 2 * (size_t)c.y);
                 hi_b = __ldcg(a.nodes32 + 2 * (size_t)c.y + 1);
                 lo_b.x = clear_sign(lo_b.x);
             } else {
-                lo_b = hi_b = __ldcg(a.leaves + ~c.y);
+                leaf_box<F64>(a, ~c.y, lo_b, hi_b);
             }
         }
         fit_compute<WIDE, F32>(a, node, r, c, rope, bl, br, lo_a, hi_a, lo_b, hi_b, nullptr, nullptr, nullptr);
@@ -482,7 +531,7 @@ __device__ __forceinline__ void fit_climb(const BuildArgs &a, int node, int hi)
     }
 }
 
-template <bool WIDE, bool F32>
+template <bool WIDE, bool F32, bool F64>
 __global__ void __launch_bounds__(kBlock) fit_kernel(const BuildArgs a)
 {
     __shared__ int s_done[kBlock];                  // local internal node b0 + t settled
@@ -490,7 +539,8 @@ __global__ void __launch_bounds__(kBlock) fit_kernel(const BuildArgs a)
     __shared__ uint2 s_lq[kBlock];                  // quantized box of leaf b0 + t
     __shared__ float4 s_lo[F32 ? kBlock : 1];       // FP32 box of internal node b0 + t
     __shared__ float4 s_hi[F32 ? kBlock : 1];
-    __shared__ float4 s_leaf[F32 ? kBlock : 1];     // FP32 position of leaf b0 + t
+    __shared__ float4 s_leaf[F32 ? kBlock : 1];     // FP32 box of leaf b0 + t: lower corner
+    __shared__ float4 s_leafhi[F32 && F64 ? kBlock : 1];   // upper corner (double-precision data)
     const int t = threadIdx.x;
     const int b0 = blockIdx.x * kBlock;
     const int b1 = min(b0 + kBlock, a.n) - 1;
@@ -513,17 +563,37 @@ __global__ void __launch_bounds__(kBlock) fit_kernel(const BuildArgs a)
             atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
             orig = 0;
         }
-        const float4 p = __ldg(a.pos + orig);
+        // the leaf's box: the FP32 point, or for double-precision data the
+        // outward-rounded box [rd(x), ru(x)] with the nearest FP32 point as
+        // the leaf word the traversal tests first
+        float3 blo, bhi, mid;
+        if (F64) {
+            double3 x64;
+            read_pos64(a, orig, blo, bhi, mid, x64);
+            double4_32a w64;
+            w64.x = x64.x;
+            w64.y = x64.y;
+            w64.z = x64.z;
+            w64.w = 0.0;
+            a.leaves64[k] = w64;
+        } else {
+            const float4 p = __ldg(a.pos + orig);
+            blo = bhi = mid = make_float3(p.x, p.y, p.z);
+        }
         const int leaf_rope = rope_after(a.range, k, hi);
         const unsigned tag = (unsigned)orig | ((leaf_rope >= 0 ? 1u : 0u) << 31);
-        const float4 leaf = make_float4(p.x, p.y, p.z, __uint_as_float(tag));
+        const float4 leaf = make_float4(mid.x, mid.y, mid.z, __uint_as_float(tag));
         a.leaves[k] = leaf;
         uint2 q;
-        q.x = pack3(q_down(p.x, g.rlo[0], g.h[0]), q_down(p.y, g.rlo[1], g.h[1]), q_down(p.z, g.rlo[2], g.h[2]));
-        q.y = pack3(q_up(p.x, g.rlo[0], g.h[0]), q_up(p.y, g.rlo[1], g.h[1]), q_up(p.z, g.rlo[2], g.h[2]));
+        q.x = pack3(q_down(blo.x, g.rlo[0], g.h[0]), q_down(blo.y, g.rlo[1], g.h[1]),
+                    q_down(blo.z, g.rlo[2], g.h[2]));
+        q.y = pack3(q_up(bhi.x, g.rlo[0], g.h[0]), q_up(bhi.y, g.rlo[1], g.h[1]), q_up(bhi.z, g.rlo[2], g.h[2]));
         a.leaf_q[k] = q;
         s_lq[t] = q;
-        if (F32) s_leaf[t] = leaf;
+        if (F32) {
+            s_leaf[t] = F64 ? make_float4(blo.x, blo.y, blo.z, 0.f) : leaf;
+            if (F64) s_leafhi[t] = make_float4(bhi.x, bhi.y, bhi.z, 0.f);
+        }
         leaf_up = a.par_leaf[k];
         // internal node k exists for every leaf index of a tree but its last
         node_valid = k <= hi - 1;
@@ -553,9 +623,9 @@ __global__ void __launch_bounds__(kBlock) fit_kernel(const BuildArgs a)
                 float4 lo_a, hi_a, lo_b, hi_b;
                 if (F32) {
                     lo_a = c.x >= 0 ? s_lo[ia] : s_leaf[ia];
-                    hi_a = c.x >= 0 ? s_hi[ia] : s_leaf[ia];
+                    hi_a = c.x >= 0 ? s_hi[ia] : (F64 ? s_leafhi[ia] : s_leaf[ia]);
                     lo_b = c.y >= 0 ? s_lo[ib] : s_leaf[ib];
-                    hi_b = c.y >= 0 ? s_hi[ib] : s_leaf[ib];
+                    hi_b = c.y >= 0 ? s_hi[ib] : (F64 ? s_leafhi[ib] : s_leaf[ib]);
                 }
                 fit_compute<WIDE, F32>(a, k, r, c, rope, bl, br, lo_a, hi_a, lo_b, hi_b, &s_q[t],
                                        F32 ? &s_lo[t] : nullptr, F32 ? &s_hi[t] : nullptr);
@@ -574,13 +644,13 @@ __global__ void __launch_bounds__(kBlock) fit_kernel(const BuildArgs a)
     // decides, and a parent's range contains its child's)
     if (live && leaf_up >= 0 && leaf_up < a.n) {
         const int2 pr = a.range[leaf_up];
-        if (!(pr.x >= b0 && pr.y <= b1)) fit_climb<WIDE, F32>(a, leaf_up, hi);
+        if (!(pr.x >= b0 && pr.y <= b1)) fit_climb<WIDE, F32, F64>(a, leaf_up, hi);
     } else if (live && leaf_up >= a.n) {
         atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
     }
     if (local && up >= 0 && up < a.n) {
         const int2 pr = a.range[up];
-        if (!(pr.x >= b0 && pr.y <= b1)) fit_climb<WIDE, F32>(a, up, hi);
+        if (!(pr.x >= b0 && pr.y <= b1)) fit_climb<WIDE, F32, F64>(a, up, hi);
     } else if (local && up >= a.n) {
         atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
     }
@@ -603,9 +673,11 @@ void launch_morton(const BuildArgs &a, cudaStream_t s)
 {
     if (a.n == 0) return;
     if (a.wide_keys)
-        morton_kernel<true><<<blocks_for(a.n, kBlock), kBlock, 0, s>>>(a, a.seg_rootbits);
+        morton_kernel<true, false><<<blocks_for(a.n, kBlock), kBlock, 0, s>>>(a, a.seg_rootbits);
+    else if (a.pos64)
+        morton_kernel<false, true><<<blocks_for(a.n, kBlock), kBlock, 0, s>>>(a, a.seg_rootbits);
     else
-        morton_kernel<false><<<blocks_for(a.n, kBlock), kBlock, 0, s>>>(a, a.seg_rootbits);
+        morton_kernel<false, false><<<blocks_for(a.n, kBlock), kBlock, 0, s>>>(a, a.seg_rootbits);
 }
 
 void launch_seg_scan(const BuildArgs &a, cudaStream_t s)
@@ -627,11 +699,14 @@ void launch_fit(const BuildArgs &a, cudaStream_t s)
     if (a.n == 0) return;
     const int g = blocks_for(a.n, kBlock);
     if (a.wide_keys) {
-        if (a.nodes32) fit_kernel<true, true><<<g, kBlock, 0, s>>>(a);
-        else fit_kernel<true, false><<<g, kBlock, 0, s>>>(a);
+        if (a.nodes32) fit_kernel<true, true, false><<<g, kBlock, 0, s>>>(a);
+        else fit_kernel<true, false, false><<<g, kBlock, 0, s>>>(a);
+    } else if (a.pos64) {
+        if (a.nodes32) fit_kernel<false, true, true><<<g, kBlock, 0, s>>>(a);
+        else fit_kernel<false, false, true><<<g, kBlock, 0, s>>>(a);
     } else {
-        if (a.nodes32) fit_kernel<false, true><<<g, kBlock, 0, s>>>(a);
-        else fit_kernel<false, false><<<g, kBlock, 0, s>>>(a);
+        if (a.nodes32) fit_kernel<false, true, false><<<g, kBlock, 0, s>>>(a);
+        else fit_kernel<false, false, false><<<g, kBlock, 0, s>>>(a);
     }
 }
 

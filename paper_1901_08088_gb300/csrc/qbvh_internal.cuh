@@ -104,6 +104,9 @@ struct DevStatus {
 // ---- launchers (build.cu) ------------------------------------------------
 struct BuildArgs {
     const float4 *pos;   // [n] original order
+    const double4_32a *pos64; // [n] original order, double-precision data (or nullptr)
+    double L64;          // FP64 box edge of double-precision data
+    double4_32a *leaves64;   // [n] FP64 positions in Z-order (double-precision data)
     int n;
     int n_sys;
     int n_types;
@@ -177,6 +180,14 @@ struct QueryArgs {
     int candidates;        // 1: Alg. 1 candidates, no exact leaf test
     int traversal;         // 0: one thread per particle, 1: warp-uniform walk
     int warp_particles;    // particles per warp of the warp walk: 32, 16 or 8
+    // double-precision particle data: FP32 test outside the band
+    // [rl2_lo, rl2_hi] around r^2, FP64 test (leaves64, L64, r2_64) inside
+    int f64;
+    const double4_32a *leaves64;
+    double L64;
+    float rl2_lo[64];
+    float rl2_hi[64];
+    double r2_64[64];
     int block;
     float r_list[64];      // [a][b] list radius
     float rl2[64];         // fl(r * r)

@@ -262,6 +262,8 @@ struct Query {
     float nLx, nLy, nLz;  // image shift n L
     float px, py, pz;     // image centre fl(x_i + n L)
     float rl2;
+    float rl2_lo, rl2_hi; // double-precision data: band of the FP32 test around rl2
+    int pair;             // double-precision data: type pair of the current tree
 };
 
 // d2 of the exact test (see the header comment) for leaf position q.
@@ -292,11 +294,52 @@ __device__ __forceinline__ float exact_d2(const Query &c, const float4 q)
 #endif
 }
 
-// The exact test of leaf j under the current image.
+// Double-precision particle data (Sec. 2.2).  The list's decision is the
+// pinned FP64 expression
+//   dx = fl(xj - xi); dx = fl(dx - L rint(fl(dx Linv))), same for y, z,
+//   d2 = fl(fl(fl(dx^2) + fl(dy^2)) + fl(dz^2)) < fl(r^2),
+// taken under the walk's image without rint, as in FP32 (the argument in the
+// header comment holds with the FP64 unit roundoff).  The leaf words hold
+// the positions rounded to FP32, and the FP32 d2 of those decides whenever
+// it lies outside [rl2_lo, rl2_hi]: the host sets that band from a bound on
+// the difference of the two computations for pairs within the radius
+// (per component at most 2^-21 L, see qbvh_query), so it cannot change a
+// decision.  Inside the band the FP64 positions decide.
 template <bool SHIFT>
-__device__ __forceinline__ void exact_leaf(const Query &c, Row &out, int j, const float4 q)
+__device__ __forceinline__ double exact_d2_64(const QueryArgs &A, const Query &c, int j)
 {
-    if (exact_d2<SHIFT>(c, q) < c.rl2 && j != c.self) out.push(__float_as_int(q.w) & 0x7FFFFFFF);
+    const double2 *pj = reinterpret_cast<const double2 *>(A.leaves64 + j);
+    const double2 *pi = reinterpret_cast<const double2 *>(A.leaves64 + c.self);
+    const double2 jxy = __ldg(pj), jz = __ldg(pj + 1), ixy = __ldg(pi), iz = __ldg(pi + 1);
+    double dx = __dsub_rn(jxy.x, ixy.x);
+    double dy = __dsub_rn(jxy.y, ixy.y);
+    double dz = __dsub_rn(jz.x, iz.x);
+    if (SHIFT) {
+        const double L = A.L64;
+        if (c.nLx != 0.f) dx = __dsub_rn(dx, c.nLx > 0.f ? L : -L);
+        if (c.nLy != 0.f) dy = __dsub_rn(dy, c.nLy > 0.f ? L : -L);
+        if (c.nLz != 0.f) dz = __dsub_rn(dz, c.nLz > 0.f ? L : -L);
+    }
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// The exact decision for leaf j under the current image (j != self).
+template <bool SHIFT, bool F64>
+__device__ __forceinline__ bool exact_accept(const QueryArgs &A, const Query &c, int j, const float4 q)
+{
+    const float d2 = exact_d2<SHIFT>(c, q);
+    if (!F64) return d2 < c.rl2 && j != c.self;
+    if (j == c.self) return false;
+    if (d2 < c.rl2_lo) return true;
+    if (!(d2 <= c.rl2_hi)) return false;
+    return exact_d2_64<SHIFT>(A, c, j) < A.r2_64[c.pair];
+}
+
+// The exact test of leaf j under the current image.
+template <bool SHIFT, bool F64>
+__device__ __forceinline__ void exact_leaf(const QueryArgs &A, const Query &c, Row &out, int j, const float4 q)
+{
+    if (exact_accept<SHIFT, F64>(A, c, j, q)) out.push(__float_as_int(q.w) & 0x7FFFFFFF);
 }
 
 // Alg. 1 without the exact filter: list j when the sphere overlaps its
@@ -307,25 +350,25 @@ __device__ __forceinline__ void candidate_leaf(const Query &c, Row &out, int j, 
     if (j != c.self && overlap_q(c.px, c.py, c.pz, lq, f, rs2)) out.push(__float_as_int(q.w) & 0x7FFFFFFF);
 }
 
-template <bool CAND, bool SHIFT = true>
+template <bool CAND, bool SHIFT = true, bool F64 = false>
 __device__ __forceinline__ void test_leaf(const QueryArgs &A, const Query &c, Row &out, int j, const float4 q,
                                           const Frame &f, float rs2)
 {
     if (CAND)
         candidate_leaf(c, out, j, q, __ldg(A.leaf_q + j), f, rs2);
     else
-        exact_leaf<SHIFT>(c, out, j, q);
+        exact_leaf<SHIFT, F64>(A, c, out, j, q);
 }
 
 // The same decisions as exact_leaf / candidate_leaf, returned instead of
 // appended (used when several lanes share one particle's row).
-template <bool CAND, bool SHIFT>
+template <bool CAND, bool SHIFT, bool F64 = false>
 __device__ __forceinline__ bool leaf_accepts(const QueryArgs &A, const Query &c, int j, const float4 q,
                                              const Frame &f, float rs2)
 {
     if (j == c.self) return false;
     if (CAND) return overlap_q(c.px, c.py, c.pz, __ldg(A.leaf_q + j), f, rs2);
-    return exact_d2<SHIFT>(c, q) < c.rl2;
+    return exact_accept<SHIFT, F64>(A, c, j, q);
 }
 
 // Append for W lanes sharing a row: the lanes of one particle are `same`
@@ -521,7 +564,7 @@ __global__ void query_thread_kernel(const __grid_constant__ QueryArgs a)
 #ifndef QBVH_SPREAD_MAX
 #define QBVH_SPREAD_MAX 16
 #endif
-template <bool SHIFT>
+template <bool SHIFT, bool F64>
 __device__ __forceinline__ void bundle_spread(const QueryArgs &a, const Query &c, Row &out, int first, int cnt,
                                               unsigned hm)
 {
@@ -554,7 +597,7 @@ __device__ __forceinline__ void bundle_spread(const QueryArgs &a, const Query &c
         t.self = c.self - lane + src;
         const int ocount = __shfl_sync(FULL, out.count, src);
         int *orow = reinterpret_cast<int *>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(out.row), src));
-        const bool acc = owner >= 0 && jv && exact_d2<SHIFT>(t, q) < c.rl2 && j != t.self;
+        const bool acc = owner >= 0 && jv && exact_accept<SHIFT, F64>(a, t, j, q);
         const unsigned m = __ballot_sync(FULL, acc);
         if (acc) {
             const int slot = ocount + __popc(m & gmask & lt);
@@ -578,7 +621,7 @@ __device__ __forceinline__ void bundle_spread(const QueryArgs &a, const Query &c
 #endif
 // ---- one warp per 32 consecutive Z-order particles ----------------------
 // The warp-uniform rope walk of one tree under one periodic image.
-template <bool CAND, int FMT, bool SHIFT, int W>
+template <bool CAND, int FMT, bool SHIFT, int W, bool F64>
 __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Row &out, const SegInfo &g,
                                           const Frame &f, int root, int last, bool on, float rs2, int wsub,
                                           unsigned same)
@@ -604,21 +647,21 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                     }
                     int j = nd.left;
                     if (W == 1 && !CAND && l - j < 32 && __popc(hm) <= QBVH_SPREAD_MAX) {
-                        bundle_spread<SHIFT>(a, c, out, j, l - j + 1, hm);
+                        bundle_spread<SHIFT, F64>(a, c, out, j, l - j + 1, hm);
                     } else if (W == 1) {
 #if QBVH_LEAF_PAIRS
                         for (; j < l; j += 2) {   // two leaves per step: two loads in flight
                             const float4 q0 = tree_ld(a.leaves + j);
                             const float4 q1 = tree_ld(a.leaves + j + 1);
                             if (on) {
-                                test_leaf<CAND, SHIFT>(a, c, out, j, q0, f, rs2);
-                                test_leaf<CAND, SHIFT>(a, c, out, j + 1, q1, f, rs2);
+                                test_leaf<CAND, SHIFT, F64>(a, c, out, j, q0, f, rs2);
+                                test_leaf<CAND, SHIFT, F64>(a, c, out, j + 1, q1, f, rs2);
                             }
                         }
 #endif
                         for (; j <= l; ++j) {
                             const float4 q = tree_ld(a.leaves + j);
-                            if (on) test_leaf<CAND, SHIFT>(a, c, out, j, q, f, rs2);
+                            if (on) test_leaf<CAND, SHIFT, F64>(a, c, out, j, q, f, rs2);
                         }
                     } else {
                         // the W lanes of a particle take every W-th leaf
@@ -628,7 +671,7 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                             int id = 0;
                             if (jj <= l) {
                                 const float4 q = tree_ld(a.leaves + jj);
-                                acc = on && leaf_accepts<CAND, SHIFT>(a, c, jj, q, f, rs2);
+                                acc = on && leaf_accepts<CAND, SHIFT, F64>(a, c, jj, q, f, rs2);
                                 id = __float_as_int(q.w) & 0x7FFFFFFF;
                             }
                             push_shared(out, acc, id, same);
@@ -645,9 +688,9 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
             const int j = ~node;
             const float4 q = tree_ld(a.leaves + j);
             if (W == 1) {
-                if (on) test_leaf<CAND, SHIFT>(a, c, out, j, q, f, rs2);
+                if (on) test_leaf<CAND, SHIFT, F64>(a, c, out, j, q, f, rs2);
             } else {
-                const bool acc = wsub == 0 && on && leaf_accepts<CAND, SHIFT>(a, c, j, q, f, rs2);
+                const bool acc = wsub == 0 && on && leaf_accepts<CAND, SHIFT, F64>(a, c, j, q, f, rs2);
                 push_shared(out, acc, __float_as_int(q.w) & 0x7FFFFFFF, same);
             }
             node = (j == last) ? QBVH_END : ((__float_as_int(q.w) < 0) ? j + 1 : ~(j + 1));
@@ -678,7 +721,7 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
 #ifndef QBVH_QUERY_SPLIT_IMAGES
 #define QBVH_QUERY_SPLIT_IMAGES 0
 #endif
-template <bool WIDE, bool CAND, int FMT, int W, bool ONE, int PHASE>
+template <bool WIDE, bool CAND, int FMT, int W, bool ONE, int PHASE, bool F64 = false>
 __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ QueryArgs a)
 {
     constexpr int G = 32 / W;
@@ -726,6 +769,11 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
             const SegInfo g = a.seg[sys * T + tb];
             if (g.count == 0) continue;
             c.rl2 = a.rl2[ta * T + tb];
+            if (F64) {
+                c.rl2_lo = a.rl2_lo[ta * T + tb];
+                c.rl2_hi = a.rl2_hi[ta * T + tb];
+                c.pair = ta * T + tb;
+            }
             const float rs2 = a.rs2[ta * T + tb];
             const Frame f = frame_of(g);
             const int root = g.count >= 2 ? g.start : ~g.start;
@@ -733,7 +781,7 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
             if (PHASE == 0) {
                 // zero image: the walk's own root test decides whether it is empty
                 set_image(c, 13, L);
-                warp_walk<CAND, FMT, false, W>(a, c, out, g, f, root, last, part, rs2, wsub, same);
+                warp_walk<CAND, FMT, false, W, F64>(a, c, out, g, f, root, last, part, rs2, wsub, same);
                 continue;
             }
             unsigned mine = part ? image_mask(me.x, me.y, me.z, L, g, rs2) : 0u;
@@ -746,9 +794,9 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
                 set_image(c, img, L);
                 const bool on = (mine >> img) & 1u;
                 if (PHASE == 2 && img == 13)
-                    warp_walk<CAND, FMT, false, W>(a, c, out, g, f, root, last, on, rs2, wsub, same);
+                    warp_walk<CAND, FMT, false, W, F64>(a, c, out, g, f, root, last, on, rs2, wsub, same);
                 else
-                    warp_walk<CAND, FMT, true, W>(a, c, out, g, f, root, last, on, rs2, wsub, same);
+                    warp_walk<CAND, FMT, true, W, F64>(a, c, out, g, f, root, last, on, rs2, wsub, same);
             }
         }
     }
@@ -807,9 +855,25 @@ static void launch_thread(const QueryArgs &a, cudaStream_t s)
     }
 }
 
+// Double-precision particle data: the exact list of one system through the
+// warp walk with one particle per lane.
+template <int FMT>
+static void launch_f64(const QueryArgs &a, cudaStream_t s)
+{
+    const int b = a.block;
+    const int grid = (int)(((long long)((a.n + 31) / 32) * 32 + b - 1) / b);
+    if (a.n_types == 1) query_warp_kernel<false, false, FMT, 1, true, 2, true><<<grid, b, 0, s>>>(a);
+    else query_warp_kernel<false, false, FMT, 1, false, 2, true><<<grid, b, 0, s>>>(a);
+}
+
 void launch_query(const QueryArgs &a, cudaStream_t s)
 {
     if (a.n == 0) return;
+    if (a.f64) {
+        if (a.node_fmt == 0) launch_f64<0>(a, s);
+        else launch_f64<1>(a, s);
+        return;
+    }
     if (a.traversal == 0) {
         if (a.node_fmt == 0) launch_thread<0>(a, s);
         else launch_thread<1>(a, s);

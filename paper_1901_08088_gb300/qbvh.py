@@ -19,7 +19,7 @@ from ._lib import QBVHError, check, lib
 __all__ = [
     "QBVHError", "NeighborList",
     "qbvh_create", "qbvh_destroy", "qbvh_set_option", "qbvh_get_option",
-    "qbvh_build", "qbvh_build_batched", "qbvh_query", "qbvh_query_async", "qbvh_query_status",
+    "qbvh_build", "qbvh_build_f64", "qbvh_build_batched", "qbvh_query", "qbvh_query_async", "qbvh_query_status",
     "nlist_get", "qbvh_tree_get", "qbvh_lj_forward", "qbvh_lj_backward", "qbvh_pack_positions",
     "qbvh_lj_forward_noalloc", "qbvh_selftest_wait_timeout", "qbvh_strerror",
 ]
@@ -91,6 +91,12 @@ def qbvh_build(h: int, pos4: torch.Tensor, L: float, n_types: int = 1, stream=No
     n = int(pos4.shape[0])
     return lib().qbvh_build(h, _ptr(pos4) if n else None, n, float(np.float32(L)), int(n_types),
                             _stream_ptr(stream))
+
+
+def qbvh_build_f64(h: int, pos4d: torch.Tensor, L: float, n_types: int = 1, stream=None) -> int:
+    """pos4d: [n, 4] float64 CUDA tensor (x, y, z, type as a whole number); L in FP64."""
+    n = int(pos4d.shape[0])
+    return lib().qbvh_build_f64(h, _ptr(pos4d) if n else None, n, float(L), int(n_types), _stream_ptr(stream))
 
 
 def qbvh_build_batched(h: int, pos4: torch.Tensor, offsets, Ls, n_types: int = 1, stream=None) -> int:
@@ -214,6 +220,13 @@ class NeighborList:
     def build(self, pos4: torch.Tensor, L: float, n_types: int = 1, stream=None):
         check(qbvh_build(self.h, pos4, L, n_types, stream), "qbvh_build")
         self.n, self.n_types, self.n_sys = int(pos4.shape[0]), int(n_types), 1
+        self.offsets = np.array([0, self.n], np.int32)
+        return self
+
+    def build_f64(self, pos4d: torch.Tensor, L: float, n_types: int = 1, stream=None):
+        """Double-precision particle data (float64 [n, 4]); the list is exact in FP64."""
+        check(qbvh_build_f64(self.h, pos4d, L, n_types, stream), "qbvh_build_f64")
+        self.n, self.n_types, self.n_sys = int(pos4d.shape[0]), int(n_types), 1
         self.offsets = np.array([0, self.n], np.int32)
         return self
 
