@@ -347,6 +347,7 @@ def run_ours(args):
             out["batched"] = run_batched(args, local)
         if not args.no_grid_compare and world == 1 and not args.n:
             out["grid_comparison"] = run_grid_comparison(args, local)
+            out["fp64_data"] = run_fp64_comparison(args, local)
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(s, samples=1)
         elif world == 1:
@@ -433,11 +434,20 @@ def run_grid_comparison(args, local):
     from paper_1901_08088_gb300 import NeighborList, _lib, autotune
 
     cases = [("paper LJ rho 0.2", 128_000, 0.2, 3.0, 0.0), ("paper LJ rho 0.8", 128_000, 0.8, 3.0, 0.0)]
+    cases += [("paper WCA rho 0.2", 128_000, 0.2, workloads.WCA_RCUT, 0.0),
+              ("paper WCA rho 0.8", 128_000, 0.8, workloads.WCA_RCUT, 0.0)]
     cases += [(f"N scan rho 0.6", n, 0.6, 3.0, 0.0) for n in (1_000, 4_096, 16_384, 65_536)]
+    cases += [("spinodal-like liquid/vapor", 1_000_000, 0.2, 3.0, 0.0)]
     cases += [("bench workload", 2_097_152, 0.8, 3.0, 0.3)]
     out = []
     for label, n, rho, rc, skin in cases:
-        s = workloads.jittered_lattice(n, rho, 0.25 if n == 2_097_152 else 0.3, seed=0, r_cut=rc, skin=skin)
+        if label.startswith("spinodal"):
+            s = workloads.spinodal_like(n, rho, seed=0, r_cut=rc, skin=skin)
+        else:
+            # WCA: liquid-like disorder (jitter half the lattice spacing), so that
+            # the short cutoff sees neighbors at rho 0.2 too
+            jit = 0.25 if n == 2_097_152 else (0.5 * (1.0 / rho) ** (1.0 / 3.0) if "WCA" in label else 0.3)
+            s = workloads.jittered_lattice(n, rho, jit, seed=0, r_cut=rc, skin=skin)
         pos4 = torch.from_numpy(workloads.pack_float4(s.pos, s.types)).cuda()
         res = {"workload": label, "n": n, "rho": rho, "r_list": float(s.r_list[0, 0])}
         for method, space in ((0, {_lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8], _lib.QBVH_OPT_BUNDLE: [8, 16],
@@ -466,6 +476,56 @@ def run_grid_comparison(args, local):
                                                         warmup=2)
             nl.close()
         res["bvh_speedup_over_grid"] = res["grid_ms"] / res["bvh_ms"]
+        out.append(res)
+    return out
+
+
+def run_fp64_comparison(args, local):
+    """Double-precision particle data (Sec. 2.2; the paper's double-precision
+    benchmarks, Sec. 4.1-4.2): build + query of the exact FP64 list against the
+    same positions rounded to FP32, on the LJ and WCA state points (N = 128,000,
+    rho 0.2 / 0.8) and the bench workload.  Each gets a small autotune."""
+    import torch
+
+    import workloads
+    from paper_1901_08088_gb300 import NeighborList, _lib, autotune
+
+    half = lambda rho: 0.5 * (1.0 / rho) ** (1.0 / 3.0)   # liquid-like disorder for WCA
+    cases = [("LJ rho 0.2", 128_000, 0.2, 3.0, 0.0, 0.3), ("LJ rho 0.8", 128_000, 0.8, 3.0, 0.0, 0.3),
+             ("WCA rho 0.2", 128_000, 0.2, workloads.WCA_RCUT, 0.0, half(0.2)),
+             ("WCA rho 0.8", 128_000, 0.8, workloads.WCA_RCUT, 0.0, half(0.8)),
+             ("spinodal-like liquid/vapor", 1_000_000, 0.2, 3.0, 0.0, None),
+             ("bench workload", 2_097_152, 0.8, 3.0, 0.3, 0.25)]
+    space = {_lib.QBVH_OPT_BUNDLE: [16, 32, 8], _lib.QBVH_OPT_NODE_FORMAT: [1, 0]}
+    out = []
+    for label, n, rho, rc, skin, jit in cases:
+        if jit is None:
+            s64 = workloads.spinodal_like(n, rho, seed=0, r_cut=rc, skin=skin, double=True)
+        else:
+            s64 = workloads.jittered_lattice64(n, rho, jit, seed=0, r_cut=rc, skin=skin)
+        L32 = np.float32(s64.L)
+        p32 = s64.pos.astype(np.float32)
+        p32[p32 >= L32] = 0.0
+        pos4d = torch.from_numpy(workloads.pack_double4(s64.pos, s64.types)).cuda()
+        pos4 = torch.from_numpy(workloads.pack_float4(p32, s64.types)).cuda()
+        res = {"workload": label, "n": n, "rho": rho, "r_list": float(s64.r_list[0, 0])}
+        for tag, build in (("fp64", lambda nl: nl.build_f64(pos4d, s64.L)),
+                           ("fp32", lambda nl: nl.build(pos4, L32))):
+            nl = NeighborList(local)
+
+            def step(opts, nl=nl, build=build):
+                for k, v in opts.items():
+                    nl.set_option(k, v)
+                build(nl)
+                nl.query(s64.r_list, cap=CAP)
+
+            best, ms, _ = autotune.tune(step, space=space, start={k: v[0] for k, v in space.items()},
+                                        reps=5, warmup=2, sweeps=1)
+            res[f"{tag}_ms"] = ms
+            res[f"{tag}_options"] = autotune.option_names(best)
+            res[f"{tag}_mean_neighbors"] = float(nl.neighbors()[1].float().mean().item())
+            nl.close()
+        res["fp64_over_fp32_time"] = res["fp64_ms"] / res["fp32_ms"]
         out.append(res)
     return out
 

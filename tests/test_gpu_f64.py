@@ -176,3 +176,14 @@ def test_full_size_fp64_2m():
     idx = np.sort(np.random.default_rng(0).choice(s.n, 8192, replace=False))
     assert_same_lists(rg, cg, ro, co, idx=idx)
     nl.close()
+
+
+@pytest.mark.slow
+def test_spinodal_like_1m_fp64():
+    s = workloads.spinodal_like(1_000_000, 0.2, seed=0, double=True)
+    rg, cg, nl = gpu_list64(s)
+    ro, co = oracle.nlist64(s.pos, s.L, s.r_list)
+    assert np.array_equal(cg, co)
+    idx = np.sort(np.random.default_rng(1).choice(s.n, 8192, replace=False))
+    assert_same_lists(rg, cg, ro, co, idx=idx)
+    nl.close()

@@ -252,3 +252,15 @@ def test_full_size_binary_mixture():
     big = np.nonzero(s.types == 1)[0]
     assert cg[big].mean() > 100   # the large particles see their solvent shell
     nl.close()
+
+
+@pytest.mark.slow
+def test_spinodal_like_1m():
+    # the inhomogeneous liquid/vapor stand-in of Sec. 4.3, N = 10^6, r_c = 3.0
+    s = workloads.workload("spinodal_n1000000", seed=0)
+    rg, cg, nl, _ = gpu_list(s, cap=256)
+    ro, co = oracle_list(s, cap=256)
+    assert np.array_equal(cg, co)
+    idx = np.sort(np.random.default_rng(1).choice(s.n, 8192, replace=False))
+    assert_same_lists(rg, cg, ro, co, idx=idx)
+    nl.close()

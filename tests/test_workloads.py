@@ -57,3 +57,20 @@ def test_pack_float4_roundtrip():
     t = np.arange(64, dtype=np.int32) % 3
     p4 = workloads.pack_float4(s.pos, t)
     assert np.array_equal(p4[:, :3], s.pos) and np.array_equal(p4.view(np.int32)[:, 3], t)
+
+
+def test_spinodal_like_is_inhomogeneous_and_exact_in_n():
+    # a small version of the liquid/vapor stand-in (Sec. 4.3): exact N, inside
+    # the box, liquid mass fraction from the lever rule, and local densities
+    # spanning vapor to liquid
+    s = workloads.spinodal_like(60_000, 0.2, seed=1, wavelength=10.0)
+    assert s.n == 60_000 and s.pos.dtype == np.float32
+    assert (s.pos >= 0).all() and (s.pos < s.L).all()
+    frac_liquid = s.meta["n_liquid"] / s.n
+    assert abs(frac_liquid - 0.72 * (0.18 / 0.70) / 0.2) < 0.05
+    nc = 16   # cells of ~4 sigma resolve domains of wavelength 10
+    h, _ = np.histogramdd(s.pos, bins=nc, range=[(0, float(s.L))] * 3)
+    d = h.ravel() / (float(s.L) / nc) ** 3
+    assert np.percentile(d, 10) < 0.05 and np.percentile(d, 90) > 0.4
+    s64 = workloads.spinodal_like(60_000, 0.2, seed=1, wavelength=10.0, double=True)
+    assert s64.pos.dtype == np.float64 and (s64.pos < s64.L).all() and s64.n == 60_000

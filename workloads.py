@@ -18,6 +18,8 @@ not published, so seeded stand-ins with the same shapes are generated here:
 * ``two_type_lj``       -- jittered lattice with a 50/50 random type split.
 * ``jittered_lattice64`` -- the jittered lattice kept in double precision
   (the paper's double-precision particle data, Sec. 2.2, Sec. 4.1-4.2).
+* ``spinodal_like``     -- an inhomogeneous liquid/vapor configuration, the
+  stand-in for the paper's spinodal-decomposition snapshots (Sec. 4.3).
 
 Conventions (all generators):
 * FP64 arithmetic, rounded to float32 once at the end.
@@ -41,6 +43,7 @@ __all__ = [
     "jittered_lattice64",
     "pack_double4",
     "WCA_RCUT",
+    "spinodal_like",
     "box_edge",
     "jittered_lattice",
     "binary_mixture",
@@ -188,6 +191,73 @@ def jittered_lattice64(n: int, rho: float, jitter: float, seed,
                     n_types=1, r_list=_matrix(1, rl), r_cut=_matrix(1, r_cut),
                     meta=dict(kind="jittered_lattice64", n=n, rho=rho, jitter=jitter,
                               seed=seed, sites_per_axis=m, spacing=a))
+
+
+def spinodal_like(n: int = 1_000_000, rho: float = 0.2, seed=0, rho_liquid: float = 0.72,
+                  rho_vapor: float = 0.02, wavelength: float = 20.0, n_waves: int = 64,
+                  r_cut: float = 3.0, skin: float = 0.0, double: bool = False):
+    """Liquid/vapor stand-in for an LJ fluid quenched into the spinodal region
+    (Sec. 4.3: N = 10^6 at rho = 0.2, quenched to T = 0.8, where it splits into
+    liquid and vapor).  The domain pattern is Cahn's random-wave model of
+    spinodal structures: the sign of a sum of n_waves plane waves of one
+    wavelength with random directions and phases.  The field is thresholded so
+    that liquid fills the volume fraction the lever rule gives,
+    (rho - rho_vapor) / (rho_liquid - rho_vapor).  Liquid regions take the
+    sites of a jittered lattice at rho_liquid (jitter half the spacing); the
+    remaining particles are uniform in the vapor region, so N is exact.
+    Returns a System (FP32) or, with double=True, a System64.
+    """
+    rng = _rng(seed)
+    L64 = (n / rho) ** (1.0 / 3.0)
+    L32 = np.float32(L64)
+    L = float(L32) if not double else L64
+    kdir = rng.normal(size=(n_waves, 3))
+    kvec = kdir / np.linalg.norm(kdir, axis=1, keepdims=True) * (2.0 * np.pi / wavelength)
+    # periodic box: snap the wave vectors onto the box's reciprocal lattice
+    kvec = np.round(kvec * L / (2.0 * np.pi)) * (2.0 * np.pi / L)
+    phase = rng.uniform(0.0, 2.0 * np.pi, n_waves)
+
+    def field(x):
+        out = np.zeros(x.shape[0])
+        for k in range(0, n_waves, 8):
+            out += np.cos(x @ kvec[k:k + 8].T + phase[k:k + 8]).sum(1)
+        return out
+
+    phi = (rho - rho_vapor) / (rho_liquid - rho_vapor)
+    probe = rng.uniform(0.0, L, size=(200_000, 3))
+    thr = np.quantile(field(probe), 1.0 - phi)
+    # liquid: jittered lattice at rho_liquid over the box, sites in the liquid region
+    m = int(np.ceil((rho_liquid * L ** 3) ** (1.0 / 3.0)))
+    a = L / m
+    g = (np.arange(m, dtype=np.float64) + 0.5) * a
+    sites = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    sites = sites + rng.uniform(-0.5 * a, 0.5 * a, size=sites.shape)
+    liquid = sites[field(sites) > thr]
+    if liquid.shape[0] > n:
+        liquid = liquid[np.sort(rng.permutation(liquid.shape[0])[:n])]
+    # vapor: uniform in the rest of the box up to exactly n particles
+    vap = []
+    need = n - liquid.shape[0]
+    while need > 0:
+        cand = rng.uniform(0.0, L, size=(max(4 * need, 1024), 3))
+        cand = cand[field(cand) <= thr][:need]
+        vap.append(cand)
+        need -= cand.shape[0]
+    x = np.concatenate([liquid] + vap, 0)
+    x = x[rng.permutation(n)]
+    if double:
+        pos = np.mod(x, L)
+        pos[pos >= L] = 0.0
+        pos[pos < 0] = 0.0
+        rl = np.float32(np.float32(r_cut) + np.float32(skin))
+        return System64(pos=np.ascontiguousarray(pos), types=np.zeros(n, np.int32), L=L, n_types=1,
+                        r_list=_matrix(1, rl), r_cut=_matrix(1, r_cut),
+                        meta=dict(kind="spinodal_like", n=n, rho=rho, n_liquid=int(liquid.shape[0])))
+    pos = _wrap_to_f32(x, L32)
+    rl = np.float32(r_cut) + np.float32(skin)
+    return System(pos=np.ascontiguousarray(pos), types=np.zeros(n, np.int32), L=L32, n_types=1,
+                  r_list=_matrix(1, rl), r_cut=_matrix(1, r_cut),
+                  meta=dict(kind="spinodal_like", n=n, rho=rho, n_liquid=int(liquid.shape[0])))
 
 
 def _periodic_d2(a: np.ndarray, b: np.ndarray, L: float) -> np.ndarray:
@@ -343,6 +413,7 @@ WORKLOADS = {
     "mixture_L100": lambda seed=0: binary_mixture(seed),
     "ensemble_256": lambda seed=0: batched_ensemble(seed),
     "lj2type_32x65536": lambda seed=0: two_type_lj(seed),
+    "spinodal_n1000000": lambda seed=0: spinodal_like(1_000_000, 0.2, seed),
 }
 
 
