@@ -105,12 +105,12 @@ class ClockSampler:
 # the traversal sources whose SHA-256 prefix is given; any other source or options
 # report null.
 PROFILED_TRAFFIC = {
-    "source_sha256": "5b06f29dce555c48",
+    "source_sha256": "1911d4c2ae45dcb5",
     "entries": [
         {"options": {"bundle_k": 16, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
-         "bytes": 459.93e6 + 1.33e9},
+         "bytes": 458.78e6 + 1.33e9},
         {"options": {"bundle_k": 32, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
-         "bytes": 422.97e6 + 1.32e9},
+         "bytes": 420.99e6 + 1.32e9},
     ],
 }
 # kernels of one timed step: build = prepare, Morton (+ sort histograms), segment

@@ -532,7 +532,7 @@ __device__ __forceinline__ void fit_climb(const BuildArgs &a, int node, int hi)
 }
 
 template <bool WIDE, bool F32, bool F64>
-__global__ void __launch_bounds__(kBlock) fit_kernel(const BuildArgs a)
+__global__ void __launch_bounds__(kBlock, 5) fit_kernel(const BuildArgs a)
 {
     __shared__ int s_done[kBlock];                  // local internal node b0 + t settled
     __shared__ uint2 s_q[kBlock];                   // quantized box of internal node b0 + t
