@@ -100,17 +100,17 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-# DRAM bytes (read + write) of one traversal launch at N = 2,097,152, measured with
-# ncu (profiles/query_warp_kernel_lj_n2097152.md) for the options of each entry and
-# the traversal sources whose SHA-256 prefix is given; any other source or options
-# report null.
+# DRAM bytes (read + write) and warp instructions executed of one traversal launch at
+# N = 2,097,152, measured with ncu (profiles/query_warp_kernel_lj_n2097152.md) for the
+# options of each entry and the traversal sources whose SHA-256 prefix is given; any
+# other source or options report null.
 PROFILED_TRAFFIC = {
     "source_sha256": "1911d4c2ae45dcb5",
     "entries": [
         {"options": {"bundle_k": 16, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
-         "bytes": 458.78e6 + 1.33e9},
+         "bytes": 458.78e6 + 1.33e9, "warp_inst": 1964658394},
         {"options": {"bundle_k": 32, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
-         "bytes": 420.99e6 + 1.32e9},
+         "bytes": 420.99e6 + 1.32e9, "warp_inst": 1952266638},
     ],
 }
 # kernels of one timed step: build = prepare, Morton (+ sort histograms), segment
@@ -130,7 +130,7 @@ def traversal_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic(opts: dict, n: int):
+def _profiled_entry(opts: dict, n: int):
     try:
         sha = traversal_source_hash()
     except OSError:
@@ -139,8 +139,31 @@ def _profiled_traffic(opts: dict, n: int):
         return None
     for e in PROFILED_TRAFFIC["entries"]:
         if all(opts.get(k) == v for k, v in e["options"].items()):
-            return e["bytes"]
+            return e
     return None
+
+
+def _profiled_traffic(opts: dict, n: int):
+    e = _profiled_entry(opts, n)
+    return None if e is None else e["bytes"]
+
+
+def _issue_roofline(opts: dict, n: int, query_ms: float, clocks):
+    """The traversal's binding resource is instruction issue: warp instructions
+    per launch (ncu, profiled options and sources only) over the live duration,
+    against one instruction per cycle per scheduler (4 per SM) at the SM clock
+    sampled during the timed region."""
+    import torch
+
+    e = _profiled_entry(opts, n)
+    if e is None or "warp_inst" not in e or not clocks:
+        return None
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = sms * 4 * clocks["sm_mhz"] * 1e6
+    achieved = e["warp_inst"] / (query_ms * 1e-3)
+    return {"bound": "issue", "unit": "warp instructions/s", "achieved": achieved, "peak": peak,
+            "frac": achieved / peak, "warp_inst_per_launch": e["warp_inst"], "sms": sms,
+            "schedulers_per_sm": 4, "sm_mhz": clocks["sm_mhz"]}
 
 
 def max_over_ranks(x: float) -> float:
@@ -364,6 +387,8 @@ def run_ours(args):
                 "peak_source": peak_src,
                 "alg_bytes_per_launch": bytes_q,
                 "step_frac": step_alg / hbm,
+                "issue": _issue_roofline(autotune.option_names(
+                    {k: nl.get_option(k) for k in autotune.OPTION_SPACE}), n, float(t_query.mean()), clocks),
             },
             "e2e": {"value": world * n * e2e_steps / (e2e_ms * 1e-3), "unit": "particles/s",
                     "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 12 * n + 8,
