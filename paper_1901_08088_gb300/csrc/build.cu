@@ -28,6 +28,7 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kLocalSegs = 64;
+constexpr int kMortonItems = 8;   // particles per thread of the Morton pass
 
 __device__ __forceinline__ unsigned spread10(unsigned v)
 {
@@ -101,20 +102,12 @@ __global__ void __launch_bounds__(kBlock) morton_kernel(const BuildArgs a, unsig
     __shared__ unsigned s_acc[kLocalSegs * 8];
     __shared__ unsigned s_hist[8 * 256];
     __shared__ int s_seg0, s_span;
-    const int i = blockIdx.x * kBlock + threadIdx.x;
     const int T = a.n_types;
     const int npass = a.sort_passes;
     for (int t = threadIdx.x; t < npass * 256; t += kBlock) s_hist[t] = 0u;
-    if (i < a.n) {
-        // fresh arrival counters and parent links for the fit (a missing link
-        // ends a walk instead of sending it to an arbitrary index)
-        a.visit[i] = 0;
-        a.par_int[i] = -1;
-        a.par_leaf[i] = -1;
-    }
     if (threadIdx.x == 0) {
-        int first = blockIdx.x * kBlock;
-        int last = min(first + kBlock, a.n) - 1;
+        int first = blockIdx.x * kBlock * kMortonItems;
+        int last = min(first + kBlock * kMortonItems, a.n) - 1;
         int k0 = a.n_sys > 1 ? sys_of(a.sys_off, a.n_sys, first) : 0;
         int k1 = a.n_sys > 1 ? sys_of(a.sys_off, a.n_sys, last) : 0;
         s_seg0 = k0 * T;
@@ -124,6 +117,18 @@ __global__ void __launch_bounds__(kBlock) morton_kernel(const BuildArgs a, unsig
     __syncthreads();
     const bool local = s_span <= kLocalSegs;
 
+    // kMortonItems particles per thread, in kBlock-wide strides: the block's
+    // histograms and tree accumulators go to global memory once per
+    // kBlock * kMortonItems particles
+    for (int it = 0; it < kMortonItems; ++it) {
+    const int i = (blockIdx.x * kMortonItems + it) * kBlock + threadIdx.x;
+    if (i < a.n) {
+        // fresh arrival counters and parent links for the fit (a missing link
+        // ends a walk instead of sending it to an arbitrary index)
+        a.visit[i] = 0;
+        a.par_int[i] = -1;
+        a.par_leaf[i] = -1;
+    }
     unsigned err = 0u;
     int seg = -1;
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f);   // lower corner of the particle's box
@@ -207,6 +212,7 @@ __global__ void __launch_bounds__(kBlock) morton_kernel(const BuildArgs a, unsig
         atomicAdd(dst_base, v[0]);
         for (int f = 1; f <= 3; ++f) atomicMin(dst_base + f, v[f]);
         for (int f = 4; f <= 6; ++f) atomicMax(dst_base + f, v[f]);
+    }
     }
     __syncthreads();
     for (int t = threadIdx.x; t < npass * 256; t += kBlock)
@@ -673,11 +679,11 @@ void launch_morton(const BuildArgs &a, cudaStream_t s)
 {
     if (a.n == 0) return;
     if (a.wide_keys)
-        morton_kernel<true, false><<<blocks_for(a.n, kBlock), kBlock, 0, s>>>(a, a.seg_rootbits);
+        morton_kernel<true, false><<<blocks_for(a.n, kBlock * kMortonItems), kBlock, 0, s>>>(a, a.seg_rootbits);
     else if (a.pos64)
-        morton_kernel<false, true><<<blocks_for(a.n, kBlock), kBlock, 0, s>>>(a, a.seg_rootbits);
+        morton_kernel<false, true><<<blocks_for(a.n, kBlock * kMortonItems), kBlock, 0, s>>>(a, a.seg_rootbits);
     else
-        morton_kernel<false, false><<<blocks_for(a.n, kBlock), kBlock, 0, s>>>(a, a.seg_rootbits);
+        morton_kernel<false, false><<<blocks_for(a.n, kBlock * kMortonItems), kBlock, 0, s>>>(a, a.seg_rootbits);
 }
 
 void launch_seg_scan(const BuildArgs &a, cudaStream_t s)

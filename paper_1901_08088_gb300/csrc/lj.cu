@@ -228,23 +228,31 @@ __global__ void QBVH_LJ_BOUNDS lj_forward_kernel(const __grid_constant__ LJArgs 
     }
 }
 
-// One block per system: fixed-order FP64 sum of the block records.
-__global__ void lj_finalize_kernel(const double *partials, const int *sys_blk_start, int np, int T, double *U,
-                                   double *dE, double *dS)
+// One block per system: fixed-order FP64 sum of the block records.  Thread
+// t sums its own contiguous run of records in order (the loads of a run are
+// independent, so they are in flight together), then a fixed-order tree
+// adds the 1024 run sums: the same order on every call.
+constexpr int kFinThreads = 1024;
+__global__ void __launch_bounds__(kFinThreads) lj_finalize_kernel(const double *partials, const int *sys_blk_start,
+                                                                  int np, int T, double *U, double *dE, double *dS)
 {
-    __shared__ double s[256];
+    __shared__ double s[kFinThreads];
     const int sys = blockIdx.x;
+    const int t = threadIdx.x;
     const int b0 = sys_blk_start[sys], b1 = sys_blk_start[sys + 1];
+    const int run = (b1 - b0 + kFinThreads - 1) / kFinThreads;
+    const int r0 = b0 + t * run, r1 = min(r0 + run, b1);
     for (int q = 0; q < np; ++q) {
         double x = 0.0;
-        for (int b = b0 + (int)threadIdx.x; b < b1; b += blockDim.x) x += partials[(size_t)b * np + q];
-        s[threadIdx.x] = x;
+#pragma unroll 8
+        for (int b = r0; b < r1; ++b) x += partials[(size_t)b * np + q];
+        s[t] = x;
         __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        for (int o = kFinThreads / 2; o > 0; o >>= 1) {
+            if (t < o) s[t] += s[t + o];
             __syncthreads();
         }
-        if (threadIdx.x == 0) {
+        if (t == 0) {
             const double tot = s[0];
             if (q == 0) U[sys] = tot;
             else if (q <= T * T) { if (dE) dE[(size_t)sys * T * T + (q - 1)] = tot; }
@@ -322,7 +330,7 @@ void launch_lj_forward(const LJArgs &a, cudaStream_t s)
         }
     }
     const int T = a.n_types;
-    lj_finalize_kernel<<<a.n_sys, 256, 0, s>>>(a.partials, a.sys_blk_start, 1 + 2 * T * T, T, a.U, a.dE, a.dS);
+    lj_finalize_kernel<<<a.n_sys, kFinThreads, 0, s>>>(a.partials, a.sys_blk_start, 1 + 2 * T * T, T, a.U, a.dE, a.dS);
 }
 
 void launch_lj_backward(const double *g, const float *F, const double *dE, const double *dS, float *gpos,
