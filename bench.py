@@ -410,6 +410,8 @@ def run_ours(args):
             out["fp64_data"] = run_fp64_comparison(args, local)
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(s, samples=1)
+            if not args.n:
+                out["grad_err"] = gradient_check(local)
         elif world == 1:
             out["cpu_baseline"] = None
     nl.close()
@@ -588,6 +590,74 @@ def run_fp64_comparison(args, local):
         res["fp64_over_fp32_time"] = res["fp64_ms"] / res["fp32_ms"]
         out.append(res)
     return out
+
+
+def gradient_check(local):
+    """The differentiable LJ layer on its workload (Eq. 1 with per-type-pair
+    eps / sigma, two types, 32 systems x 65,536 particles, one batched build +
+    query): energies, forces and dU/deps, dU/dsigma through the autograd
+    wrapper, against the FP64 oracle on the oracle's own lists.  Part of the
+    CPU-baseline leg, the one bench leg that runs the oracle; also times the
+    GPU forward + backward (build and query included)."""
+    import torch
+
+    import oracle
+    import workloads
+    from paper_1901_08088_gb300 import NeighborList, lj_energy
+
+    systems = workloads.workload("lj2type_32x65536", seed=0)
+    E, S = systems[0].meta["eps"], systems[0].meta["sig"]
+    rc = 2.5
+    pos4 = torch.from_numpy(np.concatenate([workloads.pack_float4(q.pos, q.types) for q in systems])).cuda()
+    off = np.concatenate([[0], np.cumsum([q.n for q in systems])]).astype(np.int32)
+    Ls = np.array([q.L for q in systems], np.float32)
+    xyz = torch.from_numpy(np.concatenate([q.pos for q in systems])).cuda().requires_grad_(True)
+    eps = torch.tensor(E, dtype=torch.float32, device="cuda", requires_grad=True)
+    sig = torch.tensor(S, dtype=torch.float32, device="cuda", requires_grad=True)
+    nl = NeighborList(local)
+
+    def fwd_bwd():
+        for t in (xyz, eps, sig):
+            t.grad = None
+        nl.build_batched(pos4, off, Ls, n_types=2)
+        nl.query(float(systems[0].r_list[0, 0]), cap=CAP)
+        U = lj_energy(nl, xyz, eps, sig, rc, pos4=pos4)
+        U.sum().backward()
+        return U
+
+    for _ in range(2):
+        fwd_bwd()
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    a.record(stream)
+    for _ in range(reps):
+        U = fwd_bwd()
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b) / reps
+    U = U.detach().cpu().numpy()
+    gx = xyz.grad.cpu().numpy()
+    ge, gs = eps.grad.cpu().numpy(), sig.grad.cpu().numpy()
+    nl.close()
+    worst_u = worst_f = 0.0
+    dE = np.zeros((2, 2))
+    dS = np.zeros((2, 2))
+    for k, q in enumerate(systems):
+        ro, co = oracle.nlist(q.pos, q.L, q.r_list, q.types, q.n_types)
+        ref = oracle.lj_fp64(q.pos, q.types, q.L, E, S, np.float32(rc), ro, co)
+        lo, hi = off[k], off[k + 1]
+        worst_u = max(worst_u, abs(U[k] - ref["U"]) / abs(ref["U"]))
+        worst_f = max(worst_f, float(np.linalg.norm(-gx[lo:hi] - ref["F"]) / np.linalg.norm(ref["F"])))
+        dE += ref["dE"]
+        dS += ref["dS"]
+    return {"workload": "32 LJ systems x 65,536, two types, eps/sigma per type pair, r_cut 2.5, r_list 2.8",
+            "reference": "FP64 oracle on its own lists",
+            "U_rel_max": worst_u, "F_rel_max": worst_f,
+            "dU_deps_rel_max": float(np.max(np.abs(ge - dE) / np.abs(dE))),
+            "dU_dsigma_rel_max": float(np.max(np.abs(gs - dS) / np.abs(dS))),
+            "tolerance": 1e-5, "forward_backward_ms": ms,
+            "forward_backward_particles_per_s": float(off[-1]) / (ms * 1e-3)}
 
 
 def cpu_baseline(s, samples=1):
