@@ -105,12 +105,12 @@ class ClockSampler:
 # options of each entry and the traversal sources whose SHA-256 prefix is given; any
 # other source or options report null.
 PROFILED_TRAFFIC = {
-    "source_sha256": "1911d4c2ae45dcb5",
+    "source_sha256": "1e4fcc8db3a38a75",
     "entries": [
         {"options": {"bundle_k": 16, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
-         "bytes": 458.78e6 + 1.33e9, "warp_inst": 1964658394},
+         "bytes": 486.44e6 + 1.36e9, "warp_inst": 1855300460},
         {"options": {"bundle_k": 32, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
-         "bytes": 420.99e6 + 1.32e9, "warp_inst": 1952266638},
+         "bytes": 458.62e6 + 1.36e9, "warp_inst": 1797928799},
     ],
 }
 # kernels of one timed step: build = prepare, Morton (+ sort histograms), segment

@@ -323,23 +323,26 @@ __device__ __forceinline__ double exact_d2_64(const QueryArgs &A, const Query &c
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
-// The exact decision for leaf j under the current image (j != self).
-template <bool SHIFT, bool F64>
+// The exact decision for leaf j under the current image (j != self).  SELF =
+// false leaves out the self test where the caller knows j cannot be the
+// particle itself.  (Under a non-zero image the particle's own copy is never
+// accepted anyway: its difference is -nL exactly, so d2 >= L^2 > r^2.)
+template <bool SHIFT, bool F64, bool SELF = true>
 __device__ __forceinline__ bool exact_accept(const QueryArgs &A, const Query &c, int j, const float4 q)
 {
     const float d2 = exact_d2<SHIFT>(c, q);
-    if (!F64) return d2 < c.rl2 && j != c.self;
-    if (j == c.self) return false;
+    if (!F64) return d2 < c.rl2 && (!SELF || j != c.self);
+    if (SELF && j == c.self) return false;
     if (d2 < c.rl2_lo) return true;
     if (!(d2 <= c.rl2_hi)) return false;
     return exact_d2_64<SHIFT>(A, c, j) < A.r2_64[c.pair];
 }
 
 // The exact test of leaf j under the current image.
-template <bool SHIFT, bool F64>
+template <bool SHIFT, bool F64, bool SELF = true>
 __device__ __forceinline__ void exact_leaf(const QueryArgs &A, const Query &c, Row &out, int j, const float4 q)
 {
-    if (exact_accept<SHIFT, F64>(A, c, j, q)) out.push(__float_as_int(q.w) & 0x7FFFFFFF);
+    if (exact_accept<SHIFT, F64, SELF>(A, c, j, q)) out.push(__float_as_int(q.w) & 0x7FFFFFFF);
 }
 
 // Alg. 1 without the exact filter: list j when the sphere overlaps its
@@ -350,14 +353,14 @@ __device__ __forceinline__ void candidate_leaf(const Query &c, Row &out, int j, 
     if (j != c.self && overlap_q(c.px, c.py, c.pz, lq, f, rs2)) out.push(__float_as_int(q.w) & 0x7FFFFFFF);
 }
 
-template <bool CAND, bool SHIFT = true, bool F64 = false>
+template <bool CAND, bool SHIFT = true, bool F64 = false, bool SELF = true>
 __device__ __forceinline__ void test_leaf(const QueryArgs &A, const Query &c, Row &out, int j, const float4 q,
                                           const Frame &f, float rs2)
 {
     if (CAND)
         candidate_leaf(c, out, j, q, __ldg(A.leaf_q + j), f, rs2);
     else
-        exact_leaf<SHIFT, F64>(A, c, out, j, q);
+        exact_leaf<SHIFT, F64, SELF>(A, c, out, j, q);
 }
 
 // The same decisions as exact_leaf / candidate_leaf, returned instead of
@@ -564,7 +567,7 @@ __global__ void query_thread_kernel(const __grid_constant__ QueryArgs a)
 #ifndef QBVH_SPREAD_MAX
 #define QBVH_SPREAD_MAX 16
 #endif
-template <bool SHIFT, bool F64>
+template <bool SHIFT, bool F64, bool SELF>
 __device__ __forceinline__ void bundle_spread(const QueryArgs &a, const Query &c, Row &out, int first, int cnt,
                                               unsigned hm)
 {
@@ -597,7 +600,7 @@ __device__ __forceinline__ void bundle_spread(const QueryArgs &a, const Query &c
         t.self = c.self - lane + src;
         const int ocount = __shfl_sync(FULL, out.count, src);
         int *orow = reinterpret_cast<int *>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(out.row), src));
-        const bool acc = owner >= 0 && jv && exact_accept<SHIFT, F64>(a, t, j, q);
+        const bool acc = owner >= 0 && jv && exact_accept<SHIFT, F64, SELF>(a, t, j, q);
         const unsigned m = __ballot_sync(FULL, acc);
         if (acc) {
             const int slot = ocount + __popc(m & gmask & lt);
@@ -608,16 +611,37 @@ __device__ __forceinline__ void bundle_spread(const QueryArgs &a, const Query &c
     }
 }
 
+// bundle leaves tested two per step (two loads in flight; measured 2.25 ->
+// 2.20 ms at N = 2M) or one per step
+#ifndef QBVH_LEAF_PAIRS
+#define QBVH_LEAF_PAIRS 1
+#endif
+// Every lane tests every leaf j..l of a bundle (one particle per lane).
+template <bool CAND, bool SHIFT, bool F64, bool SELF>
+__device__ __forceinline__ void bundle_loop(const QueryArgs &a, const Query &c, Row &out, int j, int l,
+                                            const Frame &f, float rs2, bool on)
+{
+#if QBVH_LEAF_PAIRS
+    for (; j < l; j += 2) {   // two leaves per step: two loads in flight
+        const float4 q0 = tree_ld(a.leaves + j);
+        const float4 q1 = tree_ld(a.leaves + j + 1);
+        if (on) {
+            test_leaf<CAND, SHIFT, F64, SELF>(a, c, out, j, q0, f, rs2);
+            test_leaf<CAND, SHIFT, F64, SELF>(a, c, out, j + 1, q1, f, rs2);
+        }
+    }
+#endif
+    for (; j <= l; ++j) {
+        const float4 q = tree_ld(a.leaves + j);
+        if (on) test_leaf<CAND, SHIFT, F64, SELF>(a, c, out, j, q, f, rs2);
+    }
+}
+
 // Registers are capped so that 8 blocks of 256 threads (64 warps) fit on an
 // SM: the walk is latency-bound and more resident warps hide more of it
 // (measured 2.37 -> 2.23 ms at N = 2M despite a few spilled bytes).
 #ifndef QBVH_QUERY_MIN_BLOCKS
 #define QBVH_QUERY_MIN_BLOCKS 8
-#endif
-// bundle leaves tested two per step (two loads in flight; measured 2.25 ->
-// 2.20 ms at N = 2M) or one per step
-#ifndef QBVH_LEAF_PAIRS
-#define QBVH_LEAF_PAIRS 1
 #endif
 // ---- one warp per 32 consecutive Z-order particles ----------------------
 // The warp-uniform rope walk of one tree under one periodic image.
@@ -646,23 +670,16 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                         l = nd.left - 1;
                     }
                     int j = nd.left;
+                    // only a bundle holding one of the warp's own particles can
+                    // hand a lane its own leaf, and only under the zero image
+                    const bool self_here =
+                        !SHIFT && __any_sync(FULL, (unsigned)(c.self - j) <= (unsigned)(l - j));
                     if (W == 1 && !CAND && l - j < 32 && __popc(hm) <= QBVH_SPREAD_MAX) {
-                        bundle_spread<SHIFT, F64>(a, c, out, j, l - j + 1, hm);
+                        if (self_here) bundle_spread<SHIFT, F64, true>(a, c, out, j, l - j + 1, hm);
+                        else bundle_spread<SHIFT, F64, false>(a, c, out, j, l - j + 1, hm);
                     } else if (W == 1) {
-#if QBVH_LEAF_PAIRS
-                        for (; j < l; j += 2) {   // two leaves per step: two loads in flight
-                            const float4 q0 = tree_ld(a.leaves + j);
-                            const float4 q1 = tree_ld(a.leaves + j + 1);
-                            if (on) {
-                                test_leaf<CAND, SHIFT, F64>(a, c, out, j, q0, f, rs2);
-                                test_leaf<CAND, SHIFT, F64>(a, c, out, j + 1, q1, f, rs2);
-                            }
-                        }
-#endif
-                        for (; j <= l; ++j) {
-                            const float4 q = tree_ld(a.leaves + j);
-                            if (on) test_leaf<CAND, SHIFT, F64>(a, c, out, j, q, f, rs2);
-                        }
+                        if (self_here || CAND) bundle_loop<CAND, SHIFT, F64, true>(a, c, out, j, l, f, rs2, on);
+                        else bundle_loop<CAND, SHIFT, F64, false>(a, c, out, j, l, f, rs2, on);
                     } else {
                         // the W lanes of a particle take every W-th leaf
                         for (; j <= l; j += W) {
