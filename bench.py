@@ -408,10 +408,14 @@ def run_ours(args):
         if not args.no_grid_compare and world == 1 and not args.n:
             out["grid_comparison"] = run_grid_comparison(args, local)
             out["fp64_data"] = run_fp64_comparison(args, local)
+            out["configs"] = run_configs(args, local, hbm, float((t_build + t_query).mean()), mean_nbrs,
+                                         out.get("batched"), {k: nl.get_option(k) for k in autotune.OPTION_SPACE})
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(s, samples=1)
             if not args.n:
                 out["grad_err"] = gradient_check(local)
+                if out.get("configs"):
+                    cpu_configs(out["configs"])
         elif world == 1:
             out["cpu_baseline"] = None
     nl.close()
@@ -590,6 +594,118 @@ def run_fp64_comparison(args, local):
         res["fp64_over_fp32_time"] = res["fp64_ms"] / res["fp32_ms"]
         out.append(res)
     return out
+
+
+def _config_systems(name):
+    """The systems of one of the five configurations (a list; one entry unless batched)."""
+    import workloads
+
+    w = workloads.workload(name, seed=0)
+    return w if isinstance(w, list) else [w]
+
+
+CONFIG_NAMES = ["lj_n4096_rho0.6", "lj_n2097152_rho0.8", "mixture_L100", "ensemble_256", "lj2type_32x65536"]
+
+
+def run_configs(args, local, hbm, bench_ms, bench_nbrs, batched, options):
+    """Build + query of each of the five configurations on the GPU: particles/s
+    and the fraction of the HBM roofline of its algorithmic bytes (16 N + 4 N +
+    4 sum n_i).  Configuration 2 is the bench step's own build + query and
+    configuration 4 the batched graph measured above; the others are timed here
+    (one batched build for several systems), best of 10 after 3 warm-ups, after
+    a small autotune that starts from the bench step's choice."""
+    import torch
+
+    import workloads
+    from paper_1901_08088_gb300 import NeighborList, _lib, autotune
+
+    out = []
+    stream = torch.cuda.current_stream()
+    for name in CONFIG_NAMES:
+        systems = _config_systems(name)
+        total = sum(q.n for q in systems)
+        res = {"name": name, "n": total, "systems": len(systems)}
+        if name == "lj_n2097152_rho0.8":
+            ms = bench_ms
+            res["mean_neighbors"] = float(bench_nbrs)
+        elif name == "ensemble_256" and batched:
+            ms = batched["graph_ms"]
+        else:
+            q0 = systems[0]
+            pos4 = torch.from_numpy(np.concatenate([workloads.pack_float4(q.pos, q.types) for q in systems])).cuda()
+            off = np.concatenate([[0], np.cumsum([q.n for q in systems])]).astype(np.int32)
+            Ls = np.array([q.L for q in systems], np.float32)
+            nl = NeighborList(local)
+            cap = 512 if q0.n_types > 1 and name == "mixture_L100" else CAP
+
+            def step(opts=None):
+                for k, v in (opts or {}).items():
+                    nl.set_option(k, v)
+                if len(systems) == 1:
+                    nl.build(pos4, q0.L, q0.n_types)
+                else:
+                    nl.build_batched(pos4, off, Ls, n_types=q0.n_types)
+                nl.query(q0.r_list, cap=cap)
+
+            # a small autotune per configuration, from the bench step's choice
+            space = {_lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8], _lib.QBVH_OPT_BUNDLE: [16, 32],
+                     _lib.QBVH_OPT_NODE_FORMAT: [1, 0]}
+            best, _, _ = autotune.tune(step, space=space, start=dict(options), reps=3, warmup=1, sweeps=1)
+            res["options"] = autotune.option_names(best)
+            step(best)
+            for _ in range(2):
+                step()
+            ts = []
+            for _ in range(10):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                step()
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            ms = float(min(ts))
+            res["mean_neighbors"] = float(nl.neighbors()[1].float().mean().item())
+            nl.close()
+        res["gpu_ms"] = ms
+        res["gpu_particles_per_s"] = total / (ms * 1e-3)
+        if "mean_neighbors" in res:
+            alg = 20 * total + 4 * res["mean_neighbors"] * total
+            res["hbm_frac"] = alg / (ms * 1e-3) / 1e9 / hbm
+        out.append(res)
+    return out
+
+
+def cpu_configs(configs):
+    """The oracle's cell list (build + query) on the five configurations: all
+    host cores on the full configuration, and one thread (a child process with
+    OMP_NUM_THREADS=1) on a bounded sample of it."""
+    import oracle
+
+    samples = {"lj_n4096_rho0.6": 1, "lj_n2097152_rho0.8": 1, "mixture_L100": 1, "ensemble_256": 16,
+               "lj2type_32x65536": 2}
+    for res in configs:
+        systems = _config_systems(res["name"])
+        t0 = time.perf_counter()
+        for q in systems:
+            oracle.nlist(q.pos, q.L, q.r_list, q.types, q.n_types, cap=512)
+        res["cpu_all_cores_particles_per_s"] = res["n"] / (time.perf_counter() - t0)
+        res["cpu_cores"] = oracle.num_threads()
+        k = samples[res["name"]]
+        code = (
+            "import sys, time, numpy as np; sys.path.insert(0, %r); import oracle, workloads\n"
+            "w = workloads.workload(%r, seed=0); w = w if isinstance(w, list) else [w]; w = w[:%d]\n"
+            "if %r == 'lj_n2097152_rho0.8': w = [workloads.jittered_lattice(131072, 0.8, 0.25, 0, 3.0, 0.3)]\n"
+            "t0 = time.perf_counter()\n"
+            "for q in w: oracle.nlist(q.pos, q.L, q.r_list, q.types, q.n_types, cap=512)\n"
+            "print(sum(q.n for q in w), time.perf_counter() - t0)\n") % (ROOT, res["name"], k, res["name"])
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        try:
+            nn, tt = r.stdout.split()[-2:]
+            res["cpu_1thread_particles_per_s"] = float(nn) / float(tt)
+            res["cpu_1thread_sample_particles"] = int(nn)
+        except ValueError:
+            res["cpu_1thread_particles_per_s"] = None
 
 
 def gradient_check(local):
