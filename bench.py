@@ -806,7 +806,7 @@ def run_reference(args):
 
     Each step is a bounded sample of the workload: the same fluid (rho 0.8,
     jitter 0.25, r_list 3.3, r_cut 3.0) with N = 262,144 particles instead of
-    2,097,152, so that a run with the driver's --steps ends within minutes;
+    2,097,152, so that a run with a large --steps count ends within minutes;
     the metric is a rate (particles/s), which the sample estimates (the sample
     shrinks further for very long runs, see reference_sample_n).
     """
