@@ -107,12 +107,12 @@ class ClockSampler:
 # options of each entry and the traversal sources whose SHA-256 prefix is given; any
 # other source or options report null.
 PROFILED_TRAFFIC = {
-    "source_sha256": "1e4fcc8db3a38a75",
+    "source_sha256": "3ddd1c96bab6876d",
     "entries": [
         {"options": {"bundle_k": 16, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
-         "bytes": 486.44e6 + 1.36e9, "warp_inst": 1855300460},
+         "bytes": 487.70e6 + 1.36e9, "warp_inst": 1855300476},
         {"options": {"bundle_k": 32, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
-         "bytes": 458.62e6 + 1.36e9, "warp_inst": 1797928799},
+         "bytes": 456.92e6 + 1.36e9, "warp_inst": 1797928783},
     ],
 }
 # kernels of one timed step: build = prepare, Morton (+ sort histograms), segment

@@ -738,6 +738,9 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
 #ifndef QBVH_QUERY_SPLIT_IMAGES
 #define QBVH_QUERY_SPLIT_IMAGES 0
 #endif
+#ifndef QBVH_REVERSE_BLOCKS
+#define QBVH_REVERSE_BLOCKS 1
+#endif
 template <bool WIDE, bool CAND, int FMT, int W, bool ONE, int PHASE, bool F64 = false>
 __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ QueryArgs a)
 {
@@ -746,7 +749,14 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
     const int pidx = lane % G;
     const int wsub = lane / G;
     const unsigned same = (W == 1 ? 1u : (W == 2 ? 0x00010001u : (W == 4 ? 0x01010101u : 0x11111111u))) << pidx;
-    const int s = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G + pidx;
+    // with several types, blocks take the sorted order from its end: the last
+    // trees (in a size-asymmetric mixture the few large particles, whose warps
+    // span wide regions and walk longest) start first and overlap the rest
+    // instead of running alone at the end (mixture L = 100: 2.05 -> 1.89 ms;
+    // one type gains nothing from it, 1.84 -> 1.87 ms at N = 2M)
+    const int blk = (QBVH_REVERSE_BLOCKS && (ONE ? 1 : a.n_types) > 1) ? (int)(gridDim.x - 1 - blockIdx.x)
+                                                                        : (int)blockIdx.x;
+    const int s = ((blk * blockDim.x + threadIdx.x) >> 5) * G + pidx;
     const bool active = s < a.n;
     float4 me = make_float4(0.f, 0.f, 0.f, 0.f);
     int i_orig = 0, seg_i = -1;
