@@ -10,6 +10,8 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/qbvh.h"
 #include "qbvh_internal.cuh"
 
@@ -20,6 +22,15 @@ int lj_particles_per_block();
 }
 
 namespace {
+
+// Named host ranges around each stage for timeline tools (NVTX; header-only,
+// a no-op unless a profiler attaches).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct DevBuf {
     void *p = nullptr;
@@ -179,6 +190,7 @@ int map_dev_err(unsigned err)
 int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *off, const float *L, int n_types,
                cudaStream_t s, const void *pos64_dev = nullptr, double L64 = 0.0)
 {
+    NvtxRange range("qbvh_build");
     if (!h) return QBVH_ERR_INVALID_ARG;
     if (n < 0 || n >= (1 << 30) || n_sys < 1 || n_sys > 65536) return QBVH_ERR_INVALID_ARG;
     if (n_types < 1 || n_types > QBVH_MAX_TYPES || n_sys * n_types > 65536) return QBVH_ERR_INVALID_ARG;
@@ -381,6 +393,7 @@ int grid_enqueue(qbvh_ctx *h, const float *r_list, const float *rl2, int cap, cu
 
 int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s)
 {
+    NvtxRange range("qbvh_query");
     if (!h) return QBVH_ERR_INVALID_ARG;
     if (!h->built) return QBVH_ERR_NOT_BUILT;
     if (!r_list_host || cap < 1 || cap > (1 << 28)) return QBVH_ERR_INVALID_ARG;
@@ -699,6 +712,7 @@ int qbvh_lj_forward(qbvh_handle h, const void *pos_dev, const float *eps_dev, co
                     const float *r_cut_host, float *e_dev, double *U_dev, float *F_dev, double *dE_dev,
                     double *dS_dev, cudaStream_t stream)
 {
+    NvtxRange range("qbvh_lj_forward");
     if (!h) return QBVH_ERR_INVALID_ARG;
     if (!h->have_list) return QBVH_ERR_NOT_BUILT;
     if (!eps_dev || !sig_dev || !r_cut_host || !U_dev) return QBVH_ERR_INVALID_ARG;
@@ -774,6 +788,7 @@ int qbvh_lj_backward(qbvh_handle h, const double *g_dev, const float *F_dev, con
                      const double *dS_dev, float *grad_pos_dev, float *grad_eps_dev, float *grad_sig_dev,
                      cudaStream_t stream)
 {
+    NvtxRange range("qbvh_lj_backward");
     if (!h) return QBVH_ERR_INVALID_ARG;
     if (!h->built) return QBVH_ERR_NOT_BUILT;
     if (!g_dev) return QBVH_ERR_INVALID_ARG;
