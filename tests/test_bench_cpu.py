@@ -36,3 +36,13 @@ def test_reference_sample_is_bounded():
     # build 9 kernels (prepare, Morton, segment scan, 4 sort passes, Karras, fit),
     # one traversal, LJ forward + finalize
     assert bench.KERNELS_PER_STEP == 12
+
+
+def test_reference_arm_under_two_ranks_prints_once():
+    # launched like the multi-GPU bench: rank 0 alone runs the oracle and prints
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", "29613", os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.count('"impl": "reference"') == 1
