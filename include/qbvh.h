@@ -171,7 +171,9 @@ int qbvh_build(qbvh_handle h, const void *pos_dev, int n, float L, int n_types,
  *             value is used for the FP32 parts).
  * n_types   : 1..4.
  * The uniform-grid method and the candidate mode do not take FP64 data
- * (QBVH_ERR_INVALID_ARG).  Errors and device-side validation as qbvh_build.
+ * (QBVH_ERR_INVALID_ARG); the traversal of FP64 data is always the warp walk
+ * with 32 particles per warp (QBVH_OPT_TRAVERSAL and QBVH_OPT_WARP_PARTICLES
+ * do not apply).  Errors and device-side validation as qbvh_build.
  */
 int qbvh_build_f64(qbvh_handle h, const void *pos64_dev, int n, double L, int n_types,
                    cudaStream_t stream);
