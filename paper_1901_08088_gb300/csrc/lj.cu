@@ -21,7 +21,10 @@ namespace qbvh {
 namespace {
 
 constexpr int kLJBlock = 128;
-constexpr int kLJParticles = 256;   // particles per block, taken in rounds of kLJBlock / TPP
+#ifndef QBVH_LJ_PARTICLES
+#define QBVH_LJ_PARTICLES 256
+#endif
+constexpr int kLJParticles = QBVH_LJ_PARTICLES;   // particles per block, taken in rounds of kLJBlock / TPP
 
 __device__ __forceinline__ float mi_component(float d, float L, float Linv)
 {
