@@ -124,7 +124,10 @@ int qbvh_destroy(qbvh_handle h);
  * fewer particles each particle gets 32/value lanes, which split a bundle's
  * leaves and pack their accepted neighbours with a ballot.  Fewer particles
  * per warp means more warps (small systems fill the GPU) and a smaller union
- * of search spheres per walk. */
+ * of search spheres per walk.  In a single-system build of 2 to 4 types,
+ * a type of at most 4096 particles so sparse that 32 of them span more than
+ * twice its largest list radius (32 L^3 / count > (2 r_max)^3) is walked
+ * one particle per warp whatever this value. */
 #define QBVH_OPT_WARP_PARTICLES 10
 
 int qbvh_set_option(qbvh_handle h, int option, int value);

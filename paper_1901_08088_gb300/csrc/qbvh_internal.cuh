@@ -189,6 +189,7 @@ struct QueryArgs {
     float rl2_hi[64];
     double r2_64[64];
     int block;
+    int sparse_blocks;     // leading blocks that walk sparse trees one particle per warp
     float r_list[64];      // [a][b] list radius
     float rl2[64];         // fl(r * r)
     float rs[64];          // padded search radius (rounded up)

@@ -741,21 +741,120 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
 #ifndef QBVH_REVERSE_BLOCKS
 #define QBVH_REVERSE_BLOCKS 1
 #endif
+// ---- sparse trees: one particle per warp ---------------------------------
+// A tree of few, widely spaced particles (the large spheres of a
+// size-asymmetric mixture) makes poor packets: 32 consecutive Z-order
+// particles then span much of the box, so a packet walk is 32 separate
+// walks run one after another on one warp, and the few such warps end long
+// after the rest (mixture L = 100: the 400 large particles' walks of the
+// small-particle tree took 1.5 ms against 0.55 ms for all small-small
+// pairs).  Tree `ta` of a single-system FP32 build of 2 to 4 types (32-bit
+// keys) is walked one particle per warp instead when it holds at most
+// QBVH_SPARSE_MAX particles and a packet of 32 spans more than twice its
+// largest list radius:
+// 32 L^3 / count > (2 r_max)^3.  The choice changes only which warp walks a
+// particle: the walk visits the same nodes and leaves in the same order, so
+// rows are the same either way.
+#ifndef QBVH_SPARSE_TREES
+#define QBVH_SPARSE_TREES 1
+#endif
+#ifndef QBVH_SPARSE_MAX
+#define QBVH_SPARSE_MAX 4096
+#endif
+__device__ __forceinline__ bool sparse_tree(const QueryArgs &a, int ta)
+{
+    const int count = a.seg[ta].count;
+    if (count == 0 || count > QBVH_SPARSE_MAX) return false;
+    const int T = a.n_types;
+    float r = 0.f;
+    for (int tb = 0; tb < T; ++tb) r = fmaxf(r, a.r_list[ta * T + tb]);
+    const float L = a.sys[0].L, d = 2.f * r;
+    return 32.f * L * L * L > (float)count * d * d * d;
+}
+
+// The leading a.sparse_blocks blocks: every particle of a sparse tree gets a
+// whole warp (W = 32: the lanes share the walk and split each bundle's
+// leaves), warps taking particles in a grid-stride loop.
+template <int FMT>
+__device__ __forceinline__ void sparse_walks(const QueryArgs &a)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)((a.sparse_blocks * blockDim.x) >> 5);
+    const int T = a.n_types;
+    const float L = a.sys[0].L;
+    for (int ta = 0; ta < T; ++ta) {
+        if (!sparse_tree(a, ta)) continue;
+        const int start = a.seg[ta].start, count = a.seg[ta].count;
+        for (int p = gw; p < count; p += nw) {
+            const int s = start + p;
+            const float4 me = __ldg(a.leaves + s);
+            int i_orig = __float_as_int(me.w) & 0x7FFFFFFF;
+            if (i_orig >= a.n) {
+                atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
+                i_orig = s;
+            }
+            Query c;
+            c.xi = me.x;
+            c.yi = me.y;
+            c.zi = me.z;
+            c.self = s;
+            Row out;
+            out.row = a.rows + (size_t)i_orig * a.cap;
+            out.cap = a.cap;
+            out.count = 0;
+            for (int tb = 0; tb < T; ++tb) {
+                if (!(a.r_list[ta * T + tb] > 0.f)) continue;
+                const SegInfo g = a.seg[tb];
+                if (g.count == 0) continue;
+                c.rl2 = a.rl2[ta * T + tb];
+                const float rs2 = a.rs2[ta * T + tb];
+                const Frame f = frame_of(g);
+                const int root = g.count >= 2 ? g.start : ~g.start;
+                const int last = g.start + g.count - 1;
+                unsigned mask = image_mask(me.x, me.y, me.z, L, g, rs2);
+                while (mask) {
+                    const int img = __ffs(mask) - 1;
+                    mask &= mask - 1u;
+                    set_image(c, img, L);
+                    if (img == 13)
+                        warp_walk<false, FMT, false, 32, false>(a, c, out, g, f, root, last, true, rs2, lane, FULL);
+                    else
+                        warp_walk<false, FMT, true, 32, false>(a, c, out, g, f, root, last, true, rs2, lane, FULL);
+                }
+            }
+            if (lane == 0) a.counts[i_orig] = out.count;
+            warp_max_count(out.count, a.status);
+        }
+    }
+}
+
 template <bool WIDE, bool CAND, int FMT, int W, bool ONE, int PHASE, bool F64 = false>
 __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ QueryArgs a)
 {
     constexpr int G = 32 / W;
+    // sparse trees (above) exist for single-system builds with several types
+    constexpr bool SPARSE = QBVH_SPARSE_TREES && !WIDE && !ONE && !CAND && !F64 && PHASE == 2;
     const int lane = threadIdx.x & 31;
     const int pidx = lane % G;
     const int wsub = lane / G;
     const unsigned same = (W == 1 ? 1u : (W == 2 ? 0x00010001u : (W == 4 ? 0x01010101u : 0x11111111u))) << pidx;
+    int bid = (int)blockIdx.x, nblk = (int)gridDim.x;
+    if (SPARSE && a.sparse_blocks > 0) {
+        if (bid < a.sparse_blocks) {
+            sparse_walks<FMT>(a);
+            return;
+        }
+        bid -= a.sparse_blocks;
+        nblk -= a.sparse_blocks;
+    }
     // with several types, blocks take the sorted order from its end: the last
-    // trees (in a size-asymmetric mixture the few large particles, whose warps
+    // trees (in a size-asymmetric mixture the large particles, whose packets
     // span wide regions and walk longest) start first and overlap the rest
-    // instead of running alone at the end (mixture L = 100: 2.05 -> 1.89 ms;
-    // one type gains nothing from it, 1.84 -> 1.87 ms at N = 2M)
-    const int blk = (QBVH_REVERSE_BLOCKS && (ONE ? 1 : a.n_types) > 1) ? (int)(gridDim.x - 1 - blockIdx.x)
-                                                                        : (int)blockIdx.x;
+    // instead of running alone at the end (mixture L = 100: 2.05 -> 1.89 ms
+    // before sparse trees; one type gains nothing from it, 1.84 -> 1.87 ms at
+    // N = 2M)
+    const int blk = (QBVH_REVERSE_BLOCKS && (ONE ? 1 : a.n_types) > 1) ? nblk - 1 - bid : bid;
     const int s = ((blk * blockDim.x + threadIdx.x) >> 5) * G + pidx;
     const bool active = s < a.n;
     float4 me = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -779,6 +878,7 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
     out.cap = a.cap;
     out.count = (PHASE == 1 && active) ? a.counts[i_orig] : 0;
     bool walked = PHASE != 1;
+    bool elsewhere = false;   // particle of a sparse tree: walked by the leading blocks
     const int T = ONE ? 1 : a.n_types;
     // the warp's particles may belong to several trees (segment boundaries):
     // take one segment value at a time
@@ -787,6 +887,10 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
         const int seg = ONE ? 0 : __shfl_sync(FULL, seg_i, __ffs(remaining) - 1);
         const bool part = ONE ? active : (active && seg_i == seg);
         remaining = ONE ? 0u : (remaining & ~__ballot_sync(FULL, part));
+        if (SPARSE && a.sparse_blocks > 0 && sparse_tree(a, seg)) {
+            elsewhere = elsewhere || part;
+            continue;
+        }
         const int sys = seg / T;
         const int ta = seg - sys * T;
         const float L = a.sys[sys].L;
@@ -828,20 +932,38 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
         }
     }
     if (!walked) return;   // phase 1, no image to add for this warp: counts stay
-    if (active && wsub == 0) {
+    if (active && wsub == 0 && !elsewhere) {
         // the row index again (not kept live across the walk)
         int io = __float_as_int(__ldg(a.leaves + s).w) & 0x7FFFFFFF;
         a.counts[io < a.n ? io : s] = out.count;
     }
-    warp_max_count(active ? out.count : 0, a.status);
+    warp_max_count(active && !elsewhere ? out.count : 0, a.status);
 }
 
 }  // namespace
 
+// leading blocks for sparse trees: about 8 warps per SM
+static int sparse_blocks_for(const QueryArgs &a)
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || sms <= 0)
+            sms = 152;
+    }
+    return sms * (256 / a.block);
+}
+
 template <int FMT, int W, int PHASE>
-static void launch_warp_phase(const QueryArgs &a, cudaStream_t s, int grid)
+static void launch_warp_phase(QueryArgs a, cudaStream_t s, int grid)
 {
     const int b = a.block;
+    a.sparse_blocks = 0;
+    if (QBVH_SPARSE_TREES && PHASE == 2 && !a.wide_keys && !a.candidates && a.n_types > 1) {
+        a.sparse_blocks = sparse_blocks_for(a);
+        grid += a.sparse_blocks;
+    }
     if (a.wide_keys) {
         if (a.candidates) query_warp_kernel<true, true, FMT, W, false, PHASE><<<grid, b, 0, s>>>(a);
         else query_warp_kernel<true, false, FMT, W, false, PHASE><<<grid, b, 0, s>>>(a);

@@ -124,6 +124,31 @@ def test_small_binary_mixture():
     nl.close()
 
 
+@pytest.mark.parametrize("wp,block", [(32, 256), (8, 256), (32, 64)])
+def test_sparse_trees_walked_one_particle_per_warp(wp, block):
+    # Types 1 and 2 are few and widely spaced (32 L^3 / count > (2 r_max)^3,
+    # at most 4096 particles), so the kernel's leading blocks walk them one
+    # particle per warp; type 1 has more particles than those blocks have
+    # warps (152 SMs x 8), type 2 a single one, type 3 none.
+    rng = np.random.default_rng(11)
+    L = np.float32(60.0)
+    counts = [60000, 3000, 1, 0]
+    types = np.repeat(np.arange(4, dtype=np.int32), counts)
+    types = types[rng.permutation(types.size)]
+    pos = rng.uniform(0, L, size=(types.size, 3)).astype(np.float32)
+    pos[pos >= L] = 0
+    rl = np.array([[2.5, 4.0, 3.0, 2.0], [4.0, 6.0, 5.0, 2.0], [3.0, 5.0, 7.0, 2.0], [2.0, 2.0, 2.0, 2.0]],
+                  np.float32)
+    for t in (1, 2):
+        assert 32 * float(L) ** 3 / counts[t] > (2 * rl[t].max()) ** 3
+    s = workloads.System(pos=pos, types=types, L=L, n_types=4, r_list=rl, r_cut=rl.copy())
+    rg, cg, nl, _ = gpu_list(s, warp_particles=wp, block=block)
+    ro, co = oracle_list(s)
+    assert_same_lists(rg, cg, ro, co)
+    assert nl.max_count == int(co.max())
+    nl.close()
+
+
 def test_overflow_retry_and_truncation(cfg1):
     from paper_1901_08088_gb300 import _lib
 
