@@ -107,12 +107,12 @@ class ClockSampler:
 # options of each entry and the traversal sources whose SHA-256 prefix is given; any
 # other source or options report null.
 PROFILED_TRAFFIC = {
-    "source_sha256": "3ddd1c96bab6876d",
+    "source_sha256": "9c6421d6bd7549cf",
     "entries": [
         {"options": {"bundle_k": 16, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
-         "bytes": 487.70e6 + 1.36e9, "warp_inst": 1855300476},
+         "bytes": 485.28e6 + 1.36e9, "warp_inst": 1855300460},
         {"options": {"bundle_k": 32, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
-         "bytes": 456.92e6 + 1.36e9, "warp_inst": 1797928783},
+         "bytes": 455.61e6 + 1.36e9, "warp_inst": 1797928791},
     ],
 }
 # kernels of one timed step: build = prepare, Morton (+ sort histograms), segment
