@@ -659,6 +659,9 @@ def run_configs(args, local, hbm, bench_ms, bench_nbrs, batched, options):
             # a small autotune per configuration, from the bench step's choice
             space = {_lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8], _lib.QBVH_OPT_BUNDLE: [16, 32],
                      _lib.QBVH_OPT_NODE_FORMAT: [1, 0]}
+            if q0.n_types > 1 and np.all(np.asarray(q0.r_list) == np.asarray(q0.r_list).flat[0]):
+                # one radius for every type pair: one tree per system is an option
+                space[_lib.QBVH_OPT_TYPE_TREES] = [1, 0]
             best, _, _ = autotune.tune(step, space=space, start=dict(options), reps=3, warmup=1, sweeps=1)
             res["options"] = autotune.option_names(best)
             step(best)
@@ -728,7 +731,7 @@ def gradient_check(local):
 
     import oracle
     import workloads
-    from paper_1901_08088_gb300 import NeighborList, lj_energy
+    from paper_1901_08088_gb300 import NeighborList, _lib, lj_energy
 
     systems = workloads.workload("lj2type_32x65536", seed=0)
     E, S = systems[0].meta["eps"], systems[0].meta["sig"]
@@ -740,6 +743,8 @@ def gradient_check(local):
     eps = torch.tensor(E, dtype=torch.float32, device="cuda", requires_grad=True)
     sig = torch.tensor(S, dtype=torch.float32, device="cuda", requires_grad=True)
     nl = NeighborList(local)
+    # one list radius for both type pairs: one tree per system holds both types
+    nl.set_option(_lib.QBVH_OPT_TYPE_TREES, 0)
 
     def fwd_bwd():
         for t in (xyz, eps, sig):

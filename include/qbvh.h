@@ -129,6 +129,15 @@ int qbvh_destroy(qbvh_handle h);
  * twice its largest list radius (32 L^3 / count > (2 r_max)^3) is walked
  * one particle per warp whatever this value. */
 #define QBVH_OPT_WARP_PARTICLES 10
+/* Trees per system: 1 (default) = one tree per particle type, each pair of
+ * types (a, b) searched with its own radius r_list[a][b] (Sec. 1, Sec. 5);
+ * 0 = one tree per system holding every type.  With 0 the leaf test does not
+ * see types, so qbvh_query then requires the same radius for every type pair
+ * (else QBVH_ERR_INVALID_ARG); the list is the same, and each particle walks
+ * one tree instead of one per type.  Types are still validated at the build
+ * and still select the Lennard-Jones parameters.  Takes effect at the next
+ * build. */
+#define QBVH_OPT_TYPE_TREES 11
 
 int qbvh_set_option(qbvh_handle h, int option, int value);
 int qbvh_get_option(qbvh_handle h, int option, int *value);
@@ -202,7 +211,8 @@ int qbvh_build_batched(qbvh_handle h, const void *pos_dev, int n_total, int n_sy
  *
  * r_list_host : [n_types][n_types] list radii (r_cut + skin), symmetric,
  *               each 0 <= r < (L/2)(1 - 2^-20) for every system's L
- *               (0 = type pair never listed).
+ *               (0 = type pair never listed); all equal when the build
+ *               put every type in one tree (QBVH_OPT_TYPE_TREES = 0).
  * cap         : initial row capacity, >= 1; rounded up to a multiple of 4
  *               (nlist_get reports the capacity in use).
  * max_retries : when some row has more than cap neighbors the capacity is

@@ -35,6 +35,7 @@ QBVH_OPT_LJ_ZORDER = 7
 QBVH_OPT_METHOD = 8
 QBVH_OPT_GRID_LANES = 9
 QBVH_OPT_WARP_PARTICLES = 10
+QBVH_OPT_TYPE_TREES = 11
 
 _lock = threading.Lock()
 _lib = None

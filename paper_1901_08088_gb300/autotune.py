@@ -4,7 +4,9 @@ The paper lets runtime autotuners pick the kernel launch parameters during
 warm-up and then freezes them (Sec. 4).  Here the tuned options are the
 subtree-collapse size, the node format (10-bit quantized or FP32 bounds), the
 traversal mapping (thread or warp per particle), the traversal block size and
-the lanes per particle of the LJ pass.  The search is coordinate descent:
+the lanes per particle of the LJ pass; where every type pair has the same
+list radius a caller may add one tree per system instead of one per type.
+The search is coordinate descent:
 each option in turn is swept with the others held at the best values so far,
 for a fixed number of sweeps; every candidate is timed with CUDA events on
 the current stream, best of ``reps`` runs after ``warmup`` runs.
@@ -36,6 +38,7 @@ DEFAULTS = {
     _lib.QBVH_OPT_WARP_PARTICLES: 32,
     _lib.QBVH_OPT_QUERY_BLOCK: 128,
     _lib.QBVH_OPT_LJ_LANES: 2,
+    _lib.QBVH_OPT_TYPE_TREES: 1,
 }
 
 _NAMES = {
@@ -48,6 +51,7 @@ _NAMES = {
     _lib.QBVH_OPT_GRID_LANES: "grid_lanes",
     _lib.QBVH_OPT_METHOD: "method",
     _lib.QBVH_OPT_LJ_ZORDER: "lj_zorder",
+    _lib.QBVH_OPT_TYPE_TREES: "type_trees",
 }
 
 

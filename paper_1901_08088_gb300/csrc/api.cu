@@ -66,12 +66,14 @@ struct qbvh_ctx {
     int lj_zorder = 1;     // LJ pass walks particles in the tree's Z-order
     int method = 0;        // 0: quantized BVH, 1: uniform grid comparator
     int grid_tpp = 8;      // lanes per particle of the grid traversal
+    int type_trees = 1;    // 1: one tree per (system, type); 0: one tree per system
     int built_method = 0;
     const void *grid_pos = nullptr;   // positions recorded by a grid-method build
     int built_fmt = 0;     // node format of the last build
     // last build
     bool built = false;
     int n = 0, n_sys = 0, n_types = 0, n_seg = 0;
+    int tree_types = 0;   // trees per system: n_types, or 1 when all types share a tree
     bool wide = false;
     int sorted = 0;   // which key/value buffer pair holds the sorted result
     std::vector<int> off;
@@ -217,8 +219,9 @@ int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *of
     h->n = n;
     h->n_sys = n_sys;
     h->n_types = n_types;
-    h->n_seg = n_sys * n_types;
-    h->wide = (n_sys > 1) || (n_types > 4);
+    h->tree_types = h->type_trees ? n_types : 1;
+    h->n_seg = n_sys * h->tree_types;
+    h->wide = (n_sys > 1) || (h->tree_types > 4);
     h->off.assign(off, off + n_sys + 1);
     h->L.assign(L, L + n_sys);
     h->sysinfo.resize(n_sys);
@@ -250,7 +253,7 @@ int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *of
         h->built = true;
         return QBVH_OK;
     }
-    const int bits = h->wide ? 30 + ceil_log2(h->n_seg) : (n_types > 1 ? 32 : 30);
+    const int bits = h->wide ? 30 + ceil_log2(h->n_seg) : (h->tree_types > 1 ? 32 : 30);
     const int passes = (bits + 7) / 8;
     const size_t kb = h->wide ? 8 : 4;
     const size_t nn = (size_t)(n > 0 ? n : 1);
@@ -289,7 +292,8 @@ int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *of
     a.leaves64 = f64 ? reinterpret_cast<double4_32a *>(h->leaves64.p) : nullptr;
     a.n = n;
     a.n_sys = n_sys;
-    a.n_types = n_types;
+    a.n_types = h->tree_types;
+    a.type_bound = n_types;
     a.n_seg = h->n_seg;
     a.wide_keys = h->wide;
     a.bundle_k = h->bundle_k;
@@ -400,12 +404,19 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
     cap = (cap + 3) & ~3;   // rows are written in 16-byte groups
     const int T = h->n_types;
     if ((long long)h->n * cap >= (1LL << 40)) return QBVH_ERR_INVALID_ARG;
+    // all types in one tree per system: the leaf test cannot tell types
+    // apart, so every type pair must share one radius
+    const bool merged = h->built_method == 0 && h->tree_types != T;
+    if (merged)
+        for (int p = 0; p < T * T; ++p)
+            if (!(r_list_host[p] == r_list_host[0])) return QBVH_ERR_INVALID_ARG;
+    const int Tq = merged ? 1 : T;   // radius matrix of the trees
     QueryArgs q;
     memset(&q, 0, sizeof q);
     if (h->f64 && h->candidates) return QBVH_ERR_INVALID_ARG;   // exact lists only for FP64 data
     const double L_half = h->f64 ? h->L64 : (double)h->L_min;
-    for (int a = 0; a < T; ++a)
-        for (int b = 0; b < T; ++b) {
+    for (int a = 0; a < Tq; ++a)
+        for (int b = 0; b < Tq; ++b) {
             const float r = r_list_host[a * T + b];
             if (!(r >= 0.f) || !isfinite(r) || r != r_list_host[b * T + a]) return QBVH_ERR_INVALID_ARG;
             // below half the box by a relative 2^-20: then a pair is found under
@@ -424,17 +435,17 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
                 const double M = 8.0 * r64 * eps + 4.0 * eps * eps + ldexp((r64 + eps) * (r64 + eps), -20);
                 float lo = (float)(r2 - M);
                 if ((double)lo > r2 - M) lo = nextafterf(lo, -INFINITY);
-                q.rl2_lo[a * T + b] = lo;
-                q.rl2_hi[a * T + b] = round_up_f(r2 + M);
-                q.r2_64[a * T + b] = r2;
+                q.rl2_lo[a * Tq + b] = lo;
+                q.rl2_hi[a * Tq + b] = round_up_f(r2 + M);
+                q.r2_64[a * Tq + b] = r2;
             }
-            q.r_list[a * T + b] = r;
-            q.rl2[a * T + b] = r * r;
+            q.r_list[a * Tq + b] = r;
+            q.rl2[a * Tq + b] = r * r;
             // padded search radius: covers FP32 rounding of the image position
             // and of the exact test (see query.cu), rounded up
             const float rs = round_up_f((double)r * (1.0 + ldexp(1.0, -20)) + ldexp((double)h->L_max, -19));
-            q.rs[a * T + b] = rs;
-            q.rs2[a * T + b] = round_up_f((double)rs * (double)rs);
+            q.rs[a * Tq + b] = rs;
+            q.rs2[a * Tq + b] = round_up_f((double)rs * (double)rs);
         }
     DeviceGuard g(h->device);
     int rc = ensure(h, h->rows, (size_t)(h->n > 0 ? h->n : 1) * cap * 4);
@@ -450,7 +461,7 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
         rc = cuda_status();
         if (rc) return rc;
         h->cap = cap;
-        memcpy(h->r_list, q.r_list, sizeof q.r_list);
+        memcpy(h->r_list, r_list_host, sizeof(float) * T * T);
         h->have_list = true;
         return QBVH_OK;
     }
@@ -464,7 +475,7 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
     q.seg = reinterpret_cast<const SegInfo *>(h->seg.p);
     q.sys = reinterpret_cast<const SysInfo *>(h->sys.p);
     q.n = h->n;
-    q.n_types = T;
+    q.n_types = Tq;
     q.cap = cap;
     q.rows = reinterpret_cast<int *>(h->rows.p);
     q.counts = reinterpret_cast<int *>(h->counts.p);
@@ -482,7 +493,7 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
     rc = cuda_status();
     if (rc) return rc;
     h->cap = cap;
-    memcpy(h->r_list, q.r_list, sizeof q.r_list);
+    memcpy(h->r_list, r_list_host, sizeof(float) * T * T);
     h->have_list = true;
     return QBVH_OK;
 }
@@ -605,6 +616,10 @@ int qbvh_set_option(qbvh_handle h, int option, int value)
         if (value < 1 || value > 32 || (value & (value - 1))) return QBVH_ERR_INVALID_ARG;
         h->grid_tpp = value;
         return QBVH_OK;
+    case QBVH_OPT_TYPE_TREES:
+        if (value != 0 && value != 1) return QBVH_ERR_INVALID_ARG;
+        h->type_trees = value;
+        return QBVH_OK;
     default: return QBVH_ERR_INVALID_ARG;
     }
 }
@@ -623,6 +638,7 @@ int qbvh_get_option(qbvh_handle h, int option, int *value)
     case QBVH_OPT_WARP_PARTICLES: *value = h->warp_particles; return QBVH_OK;
     case QBVH_OPT_METHOD: *value = h->method; return QBVH_OK;
     case QBVH_OPT_GRID_LANES: *value = h->grid_tpp; return QBVH_OK;
+    case QBVH_OPT_TYPE_TREES: *value = h->type_trees; return QBVH_OK;
     default: return QBVH_ERR_INVALID_ARG;
     }
 }

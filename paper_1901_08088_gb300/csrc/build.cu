@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(kBlock) morton_kernel(const BuildArgs a, unsig
     __shared__ unsigned s_acc[kLocalSegs * 8];
     __shared__ unsigned s_hist[8 * 256];
     __shared__ int s_seg0, s_span;
-    const int T = a.n_types;
+    const int T = a.n_types;        // trees per system
+    const int TV = a.type_bound;    // valid types
     const int npass = a.sort_passes;
     for (int t = threadIdx.x; t < npass * 256; t += kBlock) s_hist[t] = 0u;
     if (threadIdx.x == 0) {
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(kBlock) morton_kernel(const BuildArgs a, unsig
         int type;
         if (F64) {
             const double4_32a q = a.pos64[i];
-            const bool type_ok = q.w >= 0.0 && q.w < (double)T && (double)(int)q.w == q.w;
+            const bool type_ok = q.w >= 0.0 && q.w < (double)TV && (double)(int)q.w == q.w;
             if (!type_ok) err |= QBVH_DEVERR_BAD_TYPE;
             if (!(q.x >= 0.0 && q.x < a.L64 && q.y >= 0.0 && q.y < a.L64 && q.z >= 0.0 && q.z < a.L64))
                 err |= QBVH_DEVERR_OUT_OF_BOX;
@@ -152,9 +153,9 @@ __global__ void __launch_bounds__(kBlock) morton_kernel(const BuildArgs a, unsig
         } else {
             p = __ldg(a.pos + i);
             type = __float_as_int(p.w);
-            if (type < 0 || type >= T) {
+            if (type < 0 || type >= TV) {
                 err |= QBVH_DEVERR_BAD_TYPE;
-                type = type < 0 ? 0 : T - 1;
+                type = 0;
             }
             if (!(p.x >= 0.f && p.x < sy.L && p.y >= 0.f && p.y < sy.L && p.z >= 0.f && p.z < sy.L)) {
                 err |= QBVH_DEVERR_OUT_OF_BOX;
@@ -172,6 +173,7 @@ __global__ void __launch_bounds__(kBlock) morton_kernel(const BuildArgs a, unsig
         const unsigned code = (spread10(bin_of(p.x, sy.mscale)) << 2) |
                               (spread10(bin_of(p.y, sy.mscale)) << 1) |
                               spread10(bin_of(p.z, sy.mscale));
+        if (T == 1) type = 0;   // every type in the system's one tree
         seg = k * T + type;
         const unsigned long long key = WIDE ? (((unsigned long long)seg << 30) | code)
                                             : (unsigned long long)(((unsigned)type << 30) | code);

@@ -109,7 +109,8 @@ struct BuildArgs {
     double4_32a *leaves64;   // [n] FP64 positions in Z-order (double-precision data)
     int n;
     int n_sys;
-    int n_types;
+    int n_types;         // trees per system: particle types, or 1 when all types share a tree
+    int type_bound;      // valid particle types are [0, type_bound)
     int n_seg;
     bool wide_keys;      // u64 keys
     int bundle_k;
