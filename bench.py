@@ -525,7 +525,7 @@ def run_grid_comparison(args, local):
             s = workloads.jittered_lattice(n, rho, jit, seed=0, r_cut=rc, skin=skin)
         pos4 = torch.from_numpy(workloads.pack_float4(s.pos, s.types)).cuda()
         res = {"workload": label, "n": n, "rho": rho, "r_list": float(s.r_list[0, 0])}
-        for method, space in ((0, {_lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8], _lib.QBVH_OPT_BUNDLE: [8, 16],
+        for method, space in ((0, {_lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8, 4, 1], _lib.QBVH_OPT_BUNDLE: [8, 16],
                                     _lib.QBVH_OPT_NODE_FORMAT: [1, 0]}),
                               (1, {_lib.QBVH_OPT_GRID_LANES: [2, 4, 8, 16]})):
             nl = NeighborList(local)
@@ -657,7 +657,7 @@ def run_configs(args, local, hbm, bench_ms, bench_nbrs, batched, options):
                 nl.query(q0.r_list, cap=cap)
 
             # a small autotune per configuration, from the bench step's choice
-            space = {_lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8], _lib.QBVH_OPT_BUNDLE: [16, 32],
+            space = {_lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8, 4, 1], _lib.QBVH_OPT_BUNDLE: [16, 32],
                      _lib.QBVH_OPT_NODE_FORMAT: [1, 0]}
             if q0.n_types > 1 and np.all(np.asarray(q0.r_list) == np.asarray(q0.r_list).flat[0]):
                 # one radius for every type pair: one tree per system is an option

@@ -120,8 +120,8 @@ int qbvh_destroy(qbvh_handle h);
 #define QBVH_OPT_METHOD 8
 /* Lanes per particle of the grid traversal: 1, 2, 4, 8, 16 or 32 (default 8). */
 #define QBVH_OPT_GRID_LANES 9
-/* Particles per warp of the warp-uniform walk: 32 (default), 16 or 8; with
- * fewer particles each particle gets 32/value lanes, which split a bundle's
+/* Particles per warp of the warp-uniform walk: 32 (default), 16, 8, 4, 2 or
+ * 1; with fewer particles each particle gets 32/value lanes, which split a bundle's
  * leaves and pack their accepted neighbours with a ballot.  Fewer particles
  * per warp means more warps (small systems fill the GPU) and a smaller union
  * of search spheres per walk.  In a single-system build of 2 to 4 types,

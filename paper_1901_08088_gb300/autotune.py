@@ -26,7 +26,7 @@ OPTION_SPACE = {
     _lib.QBVH_OPT_BUNDLE: [4, 8, 16, 32],
     _lib.QBVH_OPT_NODE_FORMAT: [0, 1],
     _lib.QBVH_OPT_TRAVERSAL: [1, 0],
-    _lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8],
+    _lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8, 4, 1],
     _lib.QBVH_OPT_QUERY_BLOCK: [64, 128, 256],
     _lib.QBVH_OPT_LJ_LANES: [1, 2, 4, 8],
 }

@@ -605,7 +605,7 @@ int qbvh_set_option(qbvh_handle h, int option, int value)
         h->lj_zorder = value;
         return QBVH_OK;
     case QBVH_OPT_WARP_PARTICLES:
-        if (value != 32 && value != 16 && value != 8) return QBVH_ERR_INVALID_ARG;
+        if (value < 1 || value > 32 || (value & (value - 1))) return QBVH_ERR_INVALID_ARG;
         h->warp_particles = value;
         return QBVH_OK;
     case QBVH_OPT_METHOD:

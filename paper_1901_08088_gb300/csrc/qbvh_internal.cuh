@@ -180,7 +180,7 @@ struct QueryArgs {
     DevStatus *status;
     int candidates;        // 1: Alg. 1 candidates, no exact leaf test
     int traversal;         // 0: one thread per particle, 1: warp-uniform walk
-    int warp_particles;    // particles per warp of the warp walk: 32, 16 or 8
+    int warp_particles;    // particles per warp of the warp walk: 32, 16, 8, 4, 2 or 1
     // double-precision particle data: FP32 test outside the band
     // [rl2_lo, rl2_hi] around r^2, FP64 test (leaves64, L64, r2_64) inside
     int f64;

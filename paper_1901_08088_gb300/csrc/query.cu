@@ -829,6 +829,15 @@ __device__ __forceinline__ void sparse_walks(const QueryArgs &a)
     }
 }
 
+// lanes 0, G, 2G, ... of a warp with W lanes per particle (G = 32 / W
+// particles): the lanes of particle 0
+__host__ __device__ constexpr unsigned same_lanes(int W)
+{
+    unsigned m = 0u;
+    for (int k = 0; k < W; ++k) m |= 1u << (k * (32 / W));
+    return m;
+}
+
 template <bool WIDE, bool CAND, int FMT, int W, bool ONE, int PHASE, bool F64 = false>
 __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ QueryArgs a)
 {
@@ -838,7 +847,7 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
     const int lane = threadIdx.x & 31;
     const int pidx = lane % G;
     const int wsub = lane / G;
-    const unsigned same = (W == 1 ? 1u : (W == 2 ? 0x00010001u : (W == 4 ? 0x01010101u : 0x11111111u))) << pidx;
+    const unsigned same = same_lanes(W) << pidx;
     int bid = (int)blockIdx.x, nblk = (int)gridDim.x;
     if (SPARSE && a.sparse_blocks > 0) {
         if (bid < a.sparse_blocks) {
@@ -1030,13 +1039,23 @@ void launch_query(const QueryArgs &a, cudaStream_t s)
     }
     const int W = 32 / a.warp_particles;
     if (a.node_fmt == 0) {
-        if (W == 1) launch_warp<0, 1>(a, s);
-        else if (W == 2) launch_warp<0, 2>(a, s);
-        else launch_warp<0, 4>(a, s);
+        switch (W) {
+        case 1: launch_warp<0, 1>(a, s); break;
+        case 2: launch_warp<0, 2>(a, s); break;
+        case 4: launch_warp<0, 4>(a, s); break;
+        case 8: launch_warp<0, 8>(a, s); break;
+        case 16: launch_warp<0, 16>(a, s); break;
+        default: launch_warp<0, 32>(a, s); break;
+        }
     } else {
-        if (W == 1) launch_warp<1, 1>(a, s);
-        else if (W == 2) launch_warp<1, 2>(a, s);
-        else launch_warp<1, 4>(a, s);
+        switch (W) {
+        case 1: launch_warp<1, 1>(a, s); break;
+        case 2: launch_warp<1, 2>(a, s); break;
+        case 4: launch_warp<1, 4>(a, s); break;
+        case 8: launch_warp<1, 8>(a, s); break;
+        case 16: launch_warp<1, 16>(a, s); break;
+        default: launch_warp<1, 32>(a, s); break;
+        }
     }
 }
 

@@ -36,7 +36,7 @@ def _check_systems(systems, rows, counts, off):
         assert_same_lists(rows[a:b] - a, counts[a:b], ro, co)
 
 
-@pytest.mark.parametrize("traversal,wp", [(0, 32), (1, 32), (1, 16), (1, 8)])
+@pytest.mark.parametrize("traversal,wp", [(0, 32), (1, 32), (1, 16), (1, 8), (1, 2), (1, 1)])
 def test_small_ensemble_matches_oracle_per_system(traversal, wp):
     systems = workloads.batched_ensemble(seed=5, n_sys=12, n_min=250, n_max=3000)
     rows, counts, off, nl = _batched(systems, traversal=traversal, wp=wp)
@@ -89,7 +89,7 @@ def test_ensemble_with_empty_and_single_particle_systems():
     nl.close()
 
 
-@pytest.mark.parametrize("traversal,wp", [(0, 32), (1, 32), (1, 8)])
+@pytest.mark.parametrize("traversal,wp", [(0, 32), (1, 32), (1, 8), (1, 4), (1, 1)])
 def test_two_type_batched_systems(traversal, wp):
     systems = workloads.two_type_lj(seed=8, n_sys=3, n=5000)
     rows, counts, off, nl = _batched(systems, n_types=2, traversal=traversal, wp=wp)

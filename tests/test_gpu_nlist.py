@@ -20,7 +20,7 @@ def cfg1():
 
 
 @pytest.mark.parametrize("node_format", [0, 1])
-@pytest.mark.parametrize("traversal,wp", [(0, 32), (1, 32), (1, 16), (1, 8)])
+@pytest.mark.parametrize("traversal,wp", [(0, 32), (1, 32), (1, 16), (1, 8), (1, 4), (1, 2), (1, 1)])
 @pytest.mark.parametrize("bundle,block", [(1, 128), (4, 128), (8, 64), (2, 256), (16, 128), (32, 32)])
 def test_config1_exact_list_equals_bruteforce(cfg1, bundle, block, traversal, node_format, wp):
     rg, cg, nl, _ = gpu_list(cfg1, bundle=bundle, block=block, traversal=traversal, node_format=node_format,
@@ -57,7 +57,8 @@ def _uniform(n, L, r, seed, n_types=1):
                             r_cut=rl.copy())
 
 
-@pytest.mark.parametrize("traversal,node_format,wp", [(0, 0, 32), (1, 0, 32), (1, 1, 32), (1, 0, 16), (1, 1, 8)])
+@pytest.mark.parametrize("traversal,node_format,wp", [(0, 0, 32), (1, 0, 32), (1, 1, 32), (1, 0, 16), (1, 1, 8),
+                                                     (1, 1, 4), (1, 0, 2), (1, 1, 1)])
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 31, 33, 255, 4095, 4097, 12345])
 def test_ragged_sizes(n, traversal, node_format, wp):
     L = max(8.0, (n / 0.5) ** (1 / 3))
@@ -102,7 +103,7 @@ def test_particles_on_both_faces_of_the_box():
     nl.close()
 
 
-@pytest.mark.parametrize("traversal,wp", [(0, 32), (1, 32), (1, 16), (1, 8)])
+@pytest.mark.parametrize("traversal,wp", [(0, 32), (1, 32), (1, 16), (1, 8), (1, 4), (1, 1)])
 def test_two_types_per_pair_cutoffs(traversal, wp):
     s = _uniform(20000, 30.0, 1.0, seed=5, n_types=3)
     s.r_list = np.array([[2.0, 2.5, 3.0], [2.5, 1.5, 0.0], [3.0, 0.0, 4.0]], np.float32)
@@ -124,7 +125,7 @@ def test_small_binary_mixture():
     nl.close()
 
 
-@pytest.mark.parametrize("wp,block", [(32, 256), (8, 256), (32, 64)])
+@pytest.mark.parametrize("wp,block", [(32, 256), (8, 256), (32, 64), (1, 128)])
 def test_sparse_trees_walked_one_particle_per_warp(wp, block):
     # Types 1 and 2 are few and widely spaced (32 L^3 / count > (2 r_max)^3,
     # at most 4096 particles), so the kernel's leading blocks walk them one
