@@ -107,12 +107,12 @@ class ClockSampler:
 # options of each entry and the traversal sources whose SHA-256 prefix is given; any
 # other source or options report null.
 PROFILED_TRAFFIC = {
-    "source_sha256": "9c6421d6bd7549cf",
+    "source_sha256": "f2fae501d56e292f",
     "entries": [
         {"options": {"bundle_k": 16, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
-         "bytes": 485.28e6 + 1.36e9, "warp_inst": 1855300460},
+         "bytes": 485.67e6 + 1.36e9, "warp_inst": 1855300452},
         {"options": {"bundle_k": 32, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
-         "bytes": 455.61e6 + 1.36e9, "warp_inst": 1797928791},
+         "bytes": 456.89e6 + 1.36e9, "warp_inst": 1797928799},
     ],
 }
 # kernels of one timed step: build = prepare, Morton (+ sort histograms), segment
@@ -661,7 +661,7 @@ def run_configs(args, local, hbm, bench_ms, bench_nbrs, batched, options):
                      _lib.QBVH_OPT_NODE_FORMAT: [1, 0]}
             if q0.n_types > 1 and np.all(np.asarray(q0.r_list) == np.asarray(q0.r_list).flat[0]):
                 # one radius for every type pair: one tree per system is an option
-                space[_lib.QBVH_OPT_TYPE_TREES] = [1, 0]
+                space[_lib.QBVH_OPT_TYPE_TREES] = autotune.OPTIONAL_SPACE[_lib.QBVH_OPT_TYPE_TREES]
             best, _, _ = autotune.tune(step, space=space, start=dict(options), reps=3, warmup=1, sweeps=1)
             res["options"] = autotune.option_names(best)
             step(best)

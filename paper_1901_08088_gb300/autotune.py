@@ -20,7 +20,7 @@ import torch
 
 from . import _lib
 
-__all__ = ["OPTION_SPACE", "DEFAULTS", "tune", "time_step", "option_names"]
+__all__ = ["OPTION_SPACE", "OPTIONAL_SPACE", "DEFAULTS", "tune", "time_step", "option_names"]
 
 OPTION_SPACE = {
     _lib.QBVH_OPT_BUNDLE: [4, 8, 16, 32],
@@ -29,6 +29,12 @@ OPTION_SPACE = {
     _lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8, 4, 1],
     _lib.QBVH_OPT_QUERY_BLOCK: [64, 128, 256],
     _lib.QBVH_OPT_LJ_LANES: [1, 2, 4, 8],
+}
+
+# options a caller adds to the search where they apply: one tree per system
+# only when every type pair has the same list radius
+OPTIONAL_SPACE = {
+    _lib.QBVH_OPT_TYPE_TREES: [1, 0],
 }
 
 DEFAULTS = {

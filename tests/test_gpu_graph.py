@@ -100,8 +100,9 @@ def test_autotuner_returns_a_valid_choice():
 
     best, ms, log = autotune.tune(step, reps=2, warmup=1, sweeps=1)
     assert ms > 0 and len(log) > 1
+    valid = {**autotune.OPTION_SPACE, **autotune.OPTIONAL_SPACE}
     for k, v in best.items():
-        assert v in autotune.OPTION_SPACE[k]
+        assert v in valid[k]
     # the chosen options still give the exact list
     step(best)
     torch.cuda.synchronize()
