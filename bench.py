@@ -678,6 +678,26 @@ def run_configs(args, local, hbm, bench_ms, bench_nbrs, batched, options):
             ms = float(min(ts))
             res["mean_neighbors"] = float(nl.neighbors()[1].float().mean().item())
             nl.close()
+            if len(systems) == 1 and total <= 65536:
+                # a small system is bound by launch latency: the same build +
+                # query replayed from a CUDA graph (BatchedNeighborList, one system)
+                from paper_1901_08088_gb300 import BatchedNeighborList
+
+                bl = BatchedNeighborList(pos4, off, Ls, q0.r_list, n_types=q0.n_types, cap=cap,
+                                         options=best, device=local).capture()
+                for _ in range(3):
+                    bl.replay()
+                reps = 50
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(reps):
+                    bl.replay()
+                b.record(stream)
+                b.synchronize()
+                if bl.status() == _lib.QBVH_OK:
+                    res["graph_ms"] = a.elapsed_time(b) / reps
+                    res["graph_particles_per_s"] = total / (res["graph_ms"] * 1e-3)
+                bl.close()
         res["gpu_ms"] = ms
         res["gpu_particles_per_s"] = total / (ms * 1e-3)
         if "mean_neighbors" in res:
