@@ -658,7 +658,7 @@ def run_configs(args, local, hbm, bench_ms, bench_nbrs, batched, options):
 
             # a small autotune per configuration, from the bench step's choice
             space = {_lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8, 4, 1], _lib.QBVH_OPT_BUNDLE: [16, 32],
-                     _lib.QBVH_OPT_NODE_FORMAT: [1, 0]}
+                     _lib.QBVH_OPT_NODE_FORMAT: [1, 0], _lib.QBVH_OPT_QUERY_BLOCK: [256, 128, 64]}
             if q0.n_types > 1 and np.all(np.asarray(q0.r_list) == np.asarray(q0.r_list).flat[0]):
                 # one radius for every type pair: one tree per system is an option
                 space[_lib.QBVH_OPT_TYPE_TREES] = autotune.OPTIONAL_SPACE[_lib.QBVH_OPT_TYPE_TREES]
