@@ -174,3 +174,23 @@ def test_adversarial_pairs_at_radius_match_fp64_outside_band():
     row0 = set(rows[0, : counts[0]].tolist())
     # 400 ulp closer is inside, 400 ulp farther is outside
     assert 1 in row0 and len(pts) - 1 not in row0
+
+
+@pytest.mark.parametrize("method", ["brute", "cell"])
+def test_types_do_not_matter_when_every_pair_has_one_radius(method):
+    # The definition selects j by d2 < r(t_i, t_j)^2 only, so with one radius
+    # for every type pair the typed list equals the list of the same positions
+    # with every type 0 (the property one tree per system relies on), and a
+    # zero radius for one pair removes exactly that pair's entries.
+    s = workloads.two_type_lj(seed=3, n_sys=1, n=3000)[0]
+    r = float(s.r_list[0, 0])
+    rt, ct = oracle.nlist(s.pos, s.L, np.full((2, 2), r, np.float32), s.types, 2, method=method)
+    r1, c1 = oracle.nlist(s.pos, s.L, r, method=method)
+    assert np.array_equal(ct, c1)
+    assert np.array_equal(rt, r1)
+    rz, cz = oracle.nlist(s.pos, s.L, np.array([[r, r], [r, 0.0]], np.float32), s.types, 2, method=method)
+    sets1 = oracle.rows_as_sets(r1, c1)
+    setsz = oracle.rows_as_sets(rz, cz)
+    for i in range(0, s.n, 7):
+        keep = {j for j in sets1[i] if not (s.types[i] == 1 and s.types[j] == 1)}
+        assert setsz[i] == keep
