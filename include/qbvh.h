@@ -118,7 +118,8 @@ int qbvh_destroy(qbvh_handle h);
  * the cell width is the list radius; qbvh_tree_get is not available.
  * Takes effect at the next build. */
 #define QBVH_OPT_METHOD 8
-/* Lanes per particle of the grid traversal: 1, 2, 4, 8, 16 or 32 (default 8). */
+/* Lanes per particle of the grid traversal: 1, 2, 4, 8, 16 or 32 (default 8);
+ * n * value must stay below 2^32 (else qbvh_query: QBVH_ERR_INVALID_ARG). */
 #define QBVH_OPT_GRID_LANES 9
 /* Particles per warp of the warp-uniform walk: 32 (default), 16, 8, 4, 2 or
  * 1; with fewer particles each particle gets 32/value lanes, which split a bundle's
@@ -127,7 +128,9 @@ int qbvh_destroy(qbvh_handle h);
  * of search spheres per walk.  In a single-system build of 2 to 4 types,
  * a type of at most 4096 particles so sparse that 32 of them span more than
  * twice its largest list radius (32 L^3 / count > (2 r_max)^3) is walked
- * one particle per warp whatever this value. */
+ * one particle per warp whatever this value.  The traversal launches
+ * n * 32/value threads, which must stay below 2^32 (one particle per warp:
+ * n < 2^27); qbvh_query returns QBVH_ERR_INVALID_ARG otherwise. */
 #define QBVH_OPT_WARP_PARTICLES 10
 /* Trees per system: 1 (default) = one tree per particle type, each pair of
  * types (a, b) searched with its own radius r_list[a][b] (Sec. 1, Sec. 5);

@@ -411,6 +411,12 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
         for (int p = 0; p < T * T; ++p)
             if (!(r_list_host[p] == r_list_host[0])) return QBVH_ERR_INVALID_ARG;
     const int Tq = merged ? 1 : T;   // radius matrix of the trees
+    // the traversal numbers its threads in 32 bits: n particles with 32 / p
+    // lanes each (p particles per warp, or the grid's lanes per particle)
+    // must stay below 2^32 threads, with room for the last block's rounding
+    const int lanes = h->built_method == 1 ? h->grid_tpp
+                      : (h->traversal == 1 && !h->f64) ? 32 / h->warp_particles : 1;
+    if ((long long)h->n * lanes > (1LL << 32) - 1024) return QBVH_ERR_INVALID_ARG;
     QueryArgs q;
     memset(&q, 0, sizeof q);
     if (h->f64 && h->candidates) return QBVH_ERR_INVALID_ARG;   // exact lists only for FP64 data
