@@ -18,6 +18,9 @@ Contents (C sources compiled with gcc into ``_oracle.so``):
 * ``nlist64_ref.c`` -- neighbor lists of double-precision particle data
   (Sec. 2.2): brute force and 27-cell list with one pinned FP64 decision
   expression.
+* ``cand_ref.c``  -- candidate lists of Alg. 1 without the exact leaf filter
+  (Sec. 2.3): every leaf whose quantized box the padded sphere overlaps, under
+  every periodic image whose sphere overlaps the tree's root box; brute force.
 
 Pins: every function here is checked by ``tests/test_oracle_*.py`` against
 closed forms, brute force, golden hand-derived fixtures and invariants.
@@ -33,7 +36,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_oracle.so")
-_SRCS = ["nlist_ref.c", "lbvh_ref.c", "lj_ref.c", "nlist64_ref.c"]
+_SRCS = ["nlist_ref.c", "lbvh_ref.c", "lj_ref.c", "nlist64_ref.c", "cand_ref.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -89,6 +92,8 @@ def lib():
             L.or_dequantize.restype = None
             L.or_lj_fp64.argtypes = [i32, P, P, P, f32, i32, P, P, P, i32, P, P, P, P, P, P, P]
             L.or_lj_fp64.restype = i32
+            L.or_candidates.argtypes = [i32, P, P, f32, i32, P, P, P, i32, P, P]
+            L.or_candidates.restype = i32
             _lib = L
     return _lib
 
@@ -126,6 +131,25 @@ def nlist(pos, L, r_list, types=None, n_types=1, cap=256, method="cell"):
     rc = fn(n, _p(pos), _p(types), float(np.float32(L)), n_types, _p(rl), cap, _p(rows), _p(counts))
     if rc != 0:
         raise RuntimeError(f"oracle nlist failed ({rc})")
+    return rows, counts
+
+
+def candidates(pos, L, r_list, types=None, n_types=1, cap=256):
+    """Candidate lists of Alg. 1 (no exact leaf filter, 10-bit leaf boxes, one
+    tree per type).  Returns (rows [n,cap] int32 sorted asc, counts [n] int32);
+    an index appears once per periodic image that lists it."""
+    pos = _c(pos, np.float32).reshape(-1, 3)
+    n = pos.shape[0]
+    types = np.zeros(n, np.int32) if types is None else _c(types, np.int32)
+    rl = _rl_matrix(r_list, n_types)
+    L32 = np.float32(L)
+    tree = lbvh_build(pos, types, np.full(n_types, L32, np.float32))
+    rows = np.full((n, cap), -1, np.int32)
+    counts = np.zeros(n, np.int32)
+    rc = lib().or_candidates(n, _p(pos), _p(types), float(L32), n_types, _p(rl), _p(tree["root"]),
+                             _p(tree["frame"]), cap, _p(rows), _p(counts))
+    if rc != 0:
+        raise RuntimeError(f"oracle candidates failed ({rc})")
     return rows, counts
 
 
