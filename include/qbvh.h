@@ -325,22 +325,30 @@ int qbvh_lj_backward(qbvh_handle h, const double *g_dev, const float *F_dev,
  * pos_dev, eps_dev, sig_dev, e_dev, F_dev: as for qbvh_lj_forward;
  * r_cut_host: [n_types][n_types] float32 on the host; U_dev: [1] float64;
  * dE_dev, dS_dev: [n_types][n_types] float64 (or NULL).
+ * status_dev: [1] int32 device, required: written on the stream with
+ *   QBVH_OK, QBVH_ERR_BAD_TYPE (some particle's type w is outside
+ *   [0, n_types): that particle and every pair with it are left out) or
+ *   QBVH_ERR_INTERNAL (some row entry is outside [0, n): that entry is left
+ *   out).  On either error *U_dev is NaN.  Types are not clamped.
  *
- * Nothing is allocated: the per-block FP64 sums live in a fixed array of
- * 1216 x 33 doubles (about 321 KB) inside the library, which every GPU that
- * loads the library holds until the process exits.  Limit: n_types <= 4
- * (larger counts return QBVH_ERR_INVALID_ARG because their sums would not fit
- * that array).  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress, on the current device); make that first call
- * before any stream capture.  Every call overwrites the parts of the array it
- * reads, so no clearing is needed, but calls that overlap on the GPU (several
- * streams or host threads) share the array and race.  Runs on the current
- * device.  Errors: INVALID_ARG, CUDA.
+ * Nothing is allocated: the per-block FP64 sums and the error word live in a
+ * fixed variable of 1216 x 33 doubles plus one word (about 321 KB) inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  Limit: n_types <= 4 (larger counts return QBVH_ERR_INVALID_ARG
+ * because their sums would not fit that variable).  The device address of
+ * the variable is looked up (cudaGetSymbolAddress) by the first call on each
+ * device, and again by the first call after that device's CUDA context has
+ * changed (for example after cudaDeviceReset); make such a first call before
+ * any stream capture.  Every call clears the error word and rewrites the
+ * sums it reads on its stream, so nothing carries over from one call to the
+ * next, but calls that overlap on the GPU (several streams or host threads)
+ * share the variable and race.  Runs on the current device and is
+ * asynchronous.  Errors returned: INVALID_ARG, CUDA.
  */
 int qbvh_lj_forward_noalloc(const void *pos_dev, int n, float L, int n_types, const int *rows_dev,
                             const int *counts_dev, int cap, const float *eps_dev, const float *sig_dev,
                             const float *r_cut_host, float *e_dev, double *U_dev, float *F_dev,
-                            double *dE_dev, double *dS_dev, cudaStream_t stream);
+                            double *dE_dev, double *dS_dev, int *status_dev, cudaStream_t stream);
 
 /*
  * Self-test of the bounded device-side waits (failure detection without a

@@ -65,7 +65,7 @@ SIGNATURES = {
     "qbvh_lj_forward": (I, [P, P, P, P, P, P, P, P, P, P, P]),
     "qbvh_lj_backward": (I, [P, P, P, P, P, P, P, P, P]),
     "qbvh_pack_positions": (I, [P, P, I, P, P]),
-    "qbvh_lj_forward_noalloc": (I, [P, I, F, I, P, P, I, P, P, P, P, P, P, P, P, P]),
+    "qbvh_lj_forward_noalloc": (I, [P, I, F, I, P, P, I, P, P, P, P, P, P, P, P, P, P]),
     "qbvh_selftest_wait_timeout": (I, [I, P]),
 }
 

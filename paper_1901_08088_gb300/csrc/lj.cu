@@ -49,43 +49,16 @@ __device__ __forceinline__ float mi_component(float d, float L, float Linv)
 #ifndef QBVH_LJ_F32X2
 #define QBVH_LJ_F32X2 1
 #endif
-// 1/r^2 from the hardware reciprocal (rcp.approx: at most 1 ulp, FP32
-// results stay far inside the 1e-5 relative agreement with FP64); measured
-// 0.74 -> 0.68 ms at N = 2M against the correctly rounded reciprocal.
-#ifndef QBVH_LJ_FAST_RCP
-#define QBVH_LJ_FAST_RCP 1
-#endif
-__device__ __forceinline__ float lj_rcp(float x)
-{
-#if QBVH_LJ_FAST_RCP
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-#else
-    return __frcp_rn(x);
-#endif
-}
-
 // TPP lanes share one particle: lane r of the group takes row entries
 // r, r + TPP, ..., so that a group reads its row in contiguous chunks.
 template <int T, int TPP>
 __global__ void QBVH_LJ_BOUNDS lj_forward_kernel(const __grid_constant__ LJArgs a)
 {
     constexpr int NP = 1 + 2 * T * T;
-    __shared__ float s_eps[T * T], s_sig[T * T], s_sig2[T * T], s_phic[T * T], s_dsc[T * T], s_rc2[T * T];
+    __shared__ LJParams s_par[T * T];
     __shared__ double s_red[kLJBlock / 32][NP];
     const int tid = threadIdx.x;
-    if (tid < T * T) {
-        const float e = a.eps[tid], sg = a.sig[tid];
-        s_eps[tid] = e;
-        s_sig[tid] = sg;
-        s_sig2[tid] = sg * sg;
-        s_rc2[tid] = a.rc2[tid];
-        const float sc2 = (sg * sg) / a.rc2[tid];
-        const float sc6 = sc2 * sc2 * sc2;
-        s_phic[tid] = 4.f * (sc6 * sc6 - sc6);   // shift per unit eps
-        s_dsc[tid] = 2.f * sc6 * sc6 - sc6;
-    }
+    if (tid < T * T) s_par[tid] = lj_params(a.eps[tid], a.sig[tid], a.rc2[tid]);
     __syncthreads();
     const int sys = a.blk_sys[blockIdx.x];
     const SysInfo sy = a.sys[sys];
@@ -163,22 +136,18 @@ __global__ void QBVH_LJ_BOUNDS lj_forward_kernel(const __grid_constant__ LJArgs 
                     const float r2 =
                         __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 #endif
-                    if (!(r2 < s_rc2[p])) continue;
-                    const float inv_r2 = lj_rcp(r2);
-                    const float s2 = s_sig2[p] * inv_r2;
-                    const float s6 = s2 * s2 * s2;
-                    const float uE = 4.f * (s6 * s6 - s6) - s_phic[p];   // u / eps
-                    const float q = 2.f * s6 * s6 - s6;
-                    const float w = 24.f * s_eps[p] * q * inv_r2;
-                    e += s_eps[p] * uE;
-                    fx -= w * dx;
-                    fy -= w * dy;
-                    fz -= w * dz;
+                    const LJParams &par = s_par[p];
+                    if (!(r2 < par.rc2)) continue;
+                    const LJPairTerms t = lj_pair_terms<QBVH_LJ_FAST_RCP>(r2, par);
+                    e += par.eps * t.uE;
+                    fx -= t.w * dx;
+                    fy -= t.w * dy;
+                    fz -= t.w * dz;
 #pragma unroll
                     for (int b = 0; b < T; ++b) {
                         if (b == tb) {
-                            gE[b] += uE;
-                            gS[b] += (24.f * s_eps[p] / s_sig[p]) * (q - s_dsc[p]);
+                            gE[b] += t.uE;
+                            gS[b] += t.gs;
                         }
                     }
                 }

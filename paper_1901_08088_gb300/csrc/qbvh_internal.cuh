@@ -74,6 +74,71 @@ __device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c)
 }
 
 
+// ---- Lennard-Jones pair terms (Eq. 1, truncated and shifted) -------------
+// Shared by the handle's pass (lj.cu) and the allocation-free pass
+// (noalloc.cu), so that both evaluate a pair with the same operations.
+//
+// Per type pair, from eps, sig and fl(r_c^2):
+//   sig2 = sig^2, phic = 4 (s_c^2 - s_c) with s_c = (sig^2 / r_c^2)^3 (the
+//   shift per unit eps), dsc = 2 s_c^2 - s_c (its share of dU/dsig).
+struct LJParams {
+    float eps, sig, sig2, phic, dsc, rc2;
+};
+
+__device__ __forceinline__ LJParams lj_params(float eps, float sig, float rc2)
+{
+    LJParams p;
+    p.eps = eps;
+    p.sig = sig;
+    p.sig2 = sig * sig;
+    p.rc2 = rc2;
+    const float sc2 = (sig * sig) / rc2;
+    const float sc6 = sc2 * sc2 * sc2;
+    p.phic = 4.f * (sc6 * sc6 - sc6);
+    p.dsc = 2.f * sc6 * sc6 - sc6;
+    return p;
+}
+
+// 1/r^2: the hardware reciprocal (rcp.approx, at most 1 ulp) or the
+// correctly rounded one.  QBVH_LJ_FAST_RCP = 1 (both LJ passes) takes the
+// hardware one: FP32 results stay far inside the 1e-5 relative agreement with
+// FP64, and the pass at N = 2M measured 0.74 -> 0.68 ms.
+#ifndef QBVH_LJ_FAST_RCP
+#define QBVH_LJ_FAST_RCP 1
+#endif
+template <bool FAST>
+__device__ __forceinline__ float lj_rcp(float x)
+{
+    if (FAST) {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
+    return __frcp_rn(x);
+}
+
+// The terms of one pair at squared distance r2 < rc2, s = (sig^2 / r2)^3:
+//   uE = u / eps = 4 (s^2 - s) - phic          (energy per unit eps)
+//   w  = 24 eps (2 s^2 - s) / r2               (F_i += -w d, d = x_j - x_i)
+//   gs = (24 eps / sig) ((2 s^2 - s) - dsc)    (dU/dsig of the pair)
+struct LJPairTerms {
+    float uE, w, gs;
+};
+
+template <bool FAST_RCP>
+__device__ __forceinline__ LJPairTerms lj_pair_terms(float r2, const LJParams &p)
+{
+    const float inv_r2 = lj_rcp<FAST_RCP>(r2);
+    const float s2 = p.sig2 * inv_r2;
+    const float s6 = s2 * s2 * s2;
+    LJPairTerms t;
+    t.uE = 4.f * (s6 * s6 - s6) - p.phic;
+    const float q = 2.f * s6 * s6 - s6;
+    t.w = 24.f * p.eps * q * inv_r2;
+    t.gs = (24.f * p.eps / p.sig) * (q - p.dsc);
+    return t;
+}
+
 // Per-segment (tree) information, written by the build.
 struct SegInfo {
     int start;      // first sorted position

@@ -951,17 +951,33 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
 
 }  // namespace
 
+// SM count of the current device, looked up once per device (the value
+// only sizes the sparse-tree blocks: a stale or racing read costs speed, not
+// correctness; the table is written once per slot with the same value)
+static int sm_count_current()
+{
+    constexpr int kMaxDev = 64;
+    static int sms[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        cudaGetLastError();
+        return 152;
+    }
+    int v = __atomic_load_n(&sms[dev], __ATOMIC_RELAXED);
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 152;
+        }
+        __atomic_store_n(&sms[dev], v, __ATOMIC_RELAXED);
+    }
+    return v;
+}
+
 // leading blocks for sparse trees: about 8 warps per SM
 static int sparse_blocks_for(const QueryArgs &a)
 {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-                                                      cudaSuccess || sms <= 0)
-            sms = 152;
-    }
-    return sms * (256 / a.block);
+    return sm_count_current() * (256 / a.block);
 }
 
 template <int FMT, int W, int PHASE>

@@ -158,15 +158,17 @@ def qbvh_lj_backward(h: int, g, F, dE, dS, gpos, geps, gsig, stream=None) -> int
                                   _ptr(gsig), _stream_ptr(stream))
 
 
-def qbvh_lj_forward_noalloc(pos4, L, n_types, rows, counts, eps, sig, r_cut_host, e, U, F, dE, dS,
+def qbvh_lj_forward_noalloc(pos4, L, n_types, rows, counts, eps, sig, r_cut_host, e, U, F, dE, dS, status,
                             stream=None) -> int:
-    """Allocation-free LJ pass over a caller-provided list (one system)."""
+    """Allocation-free LJ pass over a caller-provided list (one system);
+    `status` is a [1] int32 CUDA tensor that receives the device-side outcome."""
     rc = np.ascontiguousarray(np.asarray(r_cut_host, np.float32))
     n = int(pos4.shape[0])
     return lib().qbvh_lj_forward_noalloc(_ptr(pos4) if n else None, n, float(np.float32(L)), int(n_types),
                                          _ptr(rows) if n else None, _ptr(counts) if n else None,
                                          int(rows.shape[1]), _ptr(eps), _ptr(sig), rc.ctypes.data_as(C.c_void_p),
-                                         _ptr(e), _ptr(U), _ptr(F), _ptr(dE), _ptr(dS), _stream_ptr(stream))
+                                         _ptr(e), _ptr(U), _ptr(F), _ptr(dE), _ptr(dS), _ptr(status),
+                                         _stream_ptr(stream))
 
 
 def qbvh_selftest_wait_timeout(device: int = 0, stream=None) -> int:

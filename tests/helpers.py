@@ -75,3 +75,22 @@ def concat(systems):
     off = np.concatenate([[0], np.cumsum([s.n for s in systems])]).astype(np.int32)
     Ls = np.array([s.L for s in systems], np.float32)
     return pos4, off, Ls
+
+
+def assert_same_lists_chunked(rows_dev, counts_g, rows_o, counts_o, chunk=1 << 17):
+    """assert_same_lists over every row of a large list, read from the device
+    view `rows_dev` ([n, cap] tensor) in chunks of rows so that the host never
+    sorts the whole list at once."""
+    counts_g = np.asarray(counts_g)
+    counts_o = np.asarray(counts_o)
+    bad = np.nonzero(counts_g != counts_o)[0]
+    assert bad.size == 0, ("counts differ", bad[:10])
+    n = counts_o.size
+    w = int(min(max(int(counts_o.max(initial=0)), 1), rows_o.shape[1], rows_dev.shape[1]))
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        g = rows_dev[c0:c1, :w].cpu().numpy()
+        a = sorted_rows(g, counts_g[c0:c1])
+        b = sorted_rows(rows_o[c0:c1, :w], counts_o[c0:c1])
+        bad = np.nonzero((a != b).any(1))[0]
+        assert bad.size == 0, ("rows differ", (c0 + bad[:10]).tolist())

@@ -254,21 +254,6 @@ def test_handle_reuse_across_sizes():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("traversal,node_format,wp", [(0, 0, 32), (1, 0, 32), (1, 1, 32), (1, 1, 16)])
-def test_full_size_lj_2m(traversal, node_format, wp):
-    s = workloads.workload("lj_n2097152_rho0.8", seed=0)
-    rg, cg, nl, _ = gpu_list(s, traversal=traversal, node_format=node_format, warp_particles=wp)
-    ro, co = oracle_list(s)
-    rng = np.random.default_rng(0)
-    idx = np.sort(rng.choice(s.n, 8192, replace=False))
-    assert np.array_equal(cg, co)
-    assert_same_lists(rg, cg, ro, co, idx=idx)
-    nbad, bad = oracle.band_check(s.pos, s.L, s.r_list, rg, cg, sample=idx)
-    assert nbad == 0, bad
-    nl.close()
-
-
-@pytest.mark.slow
 def test_full_size_binary_mixture():
     # 400 large + 395,280 small particles, per-type trees, per-pair radii 3.4 / 5.9 / 10.4
     s = workloads.workload("mixture_L100", seed=0)
