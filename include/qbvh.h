@@ -216,7 +216,7 @@ int qbvh_build_batched(qbvh_handle h, const void *pos_dev, int n_total, int n_sy
  *               each 0 <= r < (L/2)(1 - 2^-20) for every system's L
  *               (0 = type pair never listed); all equal when the build
  *               put every type in one tree (QBVH_OPT_TYPE_TREES = 0).
- * cap         : initial row capacity, >= 1; rounded up to a multiple of 4
+ * cap         : initial row capacity, >= 1; rounded up to a multiple of 8
  *               (nlist_get reports the capacity in use).
  * max_retries : when some row has more than cap neighbors the capacity is
  *               raised to the largest count rounded up to 32 and the traversal

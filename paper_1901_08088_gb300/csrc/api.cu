@@ -401,7 +401,7 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
     if (!h) return QBVH_ERR_INVALID_ARG;
     if (!h->built) return QBVH_ERR_NOT_BUILT;
     if (!r_list_host || cap < 1 || cap > (1 << 28)) return QBVH_ERR_INVALID_ARG;
-    cap = (cap + 3) & ~3;   // rows are written in 16-byte groups
+    cap = (cap + 7) & ~7;   // rows start on 32-byte boundaries (whole sectors are written)
     const int T = h->n_types;
     if ((long long)h->n * cap >= (1LL << 40)) return QBVH_ERR_INVALID_ARG;
     // all types in one tree per system: the leaf test cannot tell types

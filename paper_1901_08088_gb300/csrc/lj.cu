@@ -26,11 +26,6 @@ constexpr int kLJBlock = 128;
 #endif
 constexpr int kLJParticles = QBVH_LJ_PARTICLES;   // particles per block, taken in rounds of kLJBlock / TPP
 
-__device__ __forceinline__ float mi_component(float d, float L, float Linv)
-{
-    return __fsub_rn(d, __fmul_rn(L, rintf(__fmul_rn(d, Linv))));
-}
-
 // register cap (0: none); caps of 10 and 12 blocks of 128 threads spill and
 // gain nothing measurable
 #ifndef QBVH_LJ_MIN_BLOCKS
@@ -44,10 +39,6 @@ __device__ __forceinline__ float mi_component(float d, float L, float Linv)
 // row entries per load: 4 (16 bytes; 2 measured 0.74 -> 0.83 ms)
 #ifndef QBVH_LJ_VEC
 #define QBVH_LJ_VEC 4
-#endif
-// x and y of the minimum-image difference as one packed f32x2 pair
-#ifndef QBVH_LJ_F32X2
-#define QBVH_LJ_F32X2 1
 #endif
 // TPP lanes share one particle: lane r of the group takes row entries
 // r, r + TPP, ..., so that a group reads its row in contiguous chunks.
@@ -117,32 +108,14 @@ __global__ void QBVH_LJ_BOUNDS lj_forward_kernel(const __grid_constant__ LJArgs 
                     int tb = T > 1 ? __float_as_int(pj.w) : 0;
                     tb = tb < 0 ? 0 : (tb >= T ? T - 1 : tb);
                     const int p = ta * T + tb;
-#if QBVH_LJ_F32X2
-                    // the same roundings as mi_component, x and y as one packed pair
-                    const f32x2 dxy0 = f2_sub(f2_pack(pj.x, pj.y), f2_pack(pi.x, pi.y));
-                    float tx, ty;
-                    f2_unpack(f2_mul(dxy0, f2_pack(sy.Linv, sy.Linv)), tx, ty);
-                    const f32x2 dxy = f2_sub(dxy0, f2_mul(f2_pack(sy.L, sy.L), f2_pack(rintf(tx), rintf(ty))));
-                    float dx, dy;
-                    f2_unpack(dxy, dx, dy);
-                    const float dz = mi_component(__fsub_rn(pj.z, pi.z), sy.L, sy.Linv);
-                    float sx, sy2;
-                    f2_unpack(f2_mul(dxy, dxy), sx, sy2);
-                    const float r2 = __fadd_rn(__fadd_rn(sx, sy2), __fmul_rn(dz, dz));
-#else
-                    const float dx = mi_component(__fsub_rn(pj.x, pi.x), sy.L, sy.Linv);
-                    const float dy = mi_component(__fsub_rn(pj.y, pi.y), sy.L, sy.Linv);
-                    const float dz = mi_component(__fsub_rn(pj.z, pi.z), sy.L, sy.Linv);
-                    const float r2 =
-                        __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-#endif
+                    const LJPairGeom gm = lj_pair_geom(pi, pj, sy.L, sy.Linv);
                     const LJParams &par = s_par[p];
-                    if (!(r2 < par.rc2)) continue;
-                    const LJPairTerms t = lj_pair_terms<QBVH_LJ_FAST_RCP>(r2, par);
+                    if (!(gm.r2 < par.rc2)) continue;
+                    const LJPairTerms t = lj_pair_terms<QBVH_LJ_FAST_RCP>(gm.vr2, par);
                     e += par.eps * t.uE;
-                    fx -= t.w * dx;
-                    fy -= t.w * dy;
-                    fz -= t.w * dz;
+                    fx -= t.w * gm.vx;
+                    fy -= t.w * gm.vy;
+                    fz -= t.w * gm.vz;
 #pragma unroll
                     for (int b = 0; b < T; ++b) {
                         if (b == tb) {

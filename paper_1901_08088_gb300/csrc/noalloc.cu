@@ -113,11 +113,6 @@ struct Rc2 {
     float v[kMaxTypes * kMaxTypes];
 };
 
-__device__ __forceinline__ float min_image(float d, float L, float Linv)
-{
-    return __fsub_rn(d, __fmul_rn(L, rintf(__fmul_rn(d, Linv))));
-}
-
 // Grid-stride over particles; each block folds its particles' contributions
 // into its own FP64 record, so the record count is fixed by the grid.  A
 // particle whose type lies outside [0, T) contributes nothing (its outputs
@@ -172,16 +167,13 @@ __global__ void __launch_bounds__(kThreads) lj_noalloc_kernel(const float4 *__re
                     continue;
                 }
                 const qbvh::LJParams &par = s_par[ta * T + tb];
-                const float dx = min_image(__fsub_rn(pj.x, pi.x), L, Linv);
-                const float dy = min_image(__fsub_rn(pj.y, pi.y), L, Linv);
-                const float dz = min_image(__fsub_rn(pj.z, pi.z), L, Linv);
-                const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-                if (!(r2 < par.rc2)) continue;
-                const qbvh::LJPairTerms t = qbvh::lj_pair_terms<QBVH_LJ_FAST_RCP>(r2, par);
+                const qbvh::LJPairGeom gm = qbvh::lj_pair_geom(pi, pj, L, Linv);
+                if (!(gm.r2 < par.rc2)) continue;
+                const qbvh::LJPairTerms t = qbvh::lj_pair_terms<QBVH_LJ_FAST_RCP>(gm.vr2, par);
                 e += par.eps * t.uE;
-                fx -= t.w * dx;
-                fy -= t.w * dy;
-                fz -= t.w * dz;
+                fx -= t.w * gm.vx;
+                fy -= t.w * gm.vy;
+                fz -= t.w * gm.vz;
 #pragma unroll
                 for (int b = 0; b < T; ++b) {
                     if (b == tb) {

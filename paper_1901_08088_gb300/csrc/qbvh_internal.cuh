@@ -39,7 +39,9 @@ namespace qbvh {
 // Packed FP32 pairs (sub/mul .rn.f32x2, sm_100 and later): each half is one
 // IEEE round-to-nearest operation, so a pair gives exactly the two scalar
 // results.  A leaf's (x, y) already lies in an aligned register pair after
-// its 16-byte load, which makes the packing free.
+// its 16-byte load, which makes the packing free.  A packed product must not
+// feed a packed add where the rounding matters: ptxas contracts that pair
+// into a fused multiply-add even with explicit .rn (scalar add.rn is kept).
 #ifndef QBVH_F32X2
 #define QBVH_F32X2 1
 #endif
@@ -137,6 +139,65 @@ __device__ __forceinline__ LJPairTerms lj_pair_terms(float r2, const LJParams &p
     t.w = 24.f * p.eps * q * inv_r2;
     t.gs = (24.f * p.eps / p.sig) * (q - p.dsc);
     return t;
+}
+
+// Geometry of one pair for the LJ passes.  Whether the pair interacts is
+// decided by the pinned FP32 minimum-image expression (the neighbor list's,
+// mirrored by the oracle): dx = fl(xj - xi); dx = fl(dx - L rint(dx Linv)),
+// r2 = fl(fl(dx^2 + dy^2) + dz^2) < fl(r_cut^2).  The pair's value takes the
+// difference rounded once instead.  For n = rint(...) != 0 the expression
+// rounds xj - xi at the magnitude of L before the shift: an absolute error up
+// to ulp(L) / 2 on a distance below r_cut, which the steep repulsion turns
+// into force errors of 1e-5 relative (two-type workload, 32 x 65,536,
+// measured 7.4e-6 normwise).  For an interacting pair with n = +1, xj > L/2,
+// so xj - L is exact (Sterbenz) and fl(fl(xj - L) - xi) rounds once; for
+// n = -1 likewise xi - L.  Those pairs (a box face between them) take this
+// branch; the others already hold the once-rounded difference.
+#ifndef QBVH_LJ_IMAGE_VALUE
+#define QBVH_LJ_IMAGE_VALUE 1
+#endif
+struct LJPairGeom {
+    float r2;                // pinned r^2 (membership)
+    float vx, vy, vz, vr2;   // difference rounded once, and fl(fl(vx^2 + vy^2) + vz^2)
+};
+
+__device__ __forceinline__ float mi_value(float xj, float xi, float n, float L)
+{
+    if (n > 0.f) return __fsub_rn(__fsub_rn(xj, L), xi);
+    if (n < 0.f) return __fsub_rn(xj, __fsub_rn(xi, L));
+    return __fsub_rn(xj, xi);
+}
+
+__device__ __forceinline__ LJPairGeom lj_pair_geom(const float4 &pi, const float4 &pj, float L, float Linv)
+{
+    // x and y as one packed pair, with the same roundings as the scalar form
+    const f32x2 dxy0 = f2_sub(f2_pack(pj.x, pj.y), f2_pack(pi.x, pi.y));
+    float tx, ty;
+    f2_unpack(f2_mul(dxy0, f2_pack(Linv, Linv)), tx, ty);
+    const float nx = rintf(tx), ny = rintf(ty);
+    // L n is exact (n in {-1, 0, 1}), so a contraction of this product and
+    // difference into one fused operation gives the same result
+    const f32x2 dxy = f2_sub(dxy0, f2_mul(f2_pack(L, L), f2_pack(nx, ny)));
+    float dx, dy;
+    f2_unpack(dxy, dx, dy);
+    const float dz0 = __fsub_rn(pj.z, pi.z);
+    const float nz = rintf(__fmul_rn(dz0, Linv));
+    const float dz = __fsub_rn(dz0, __fmul_rn(L, nz));
+    float sx, sy;
+    f2_unpack(f2_mul(dxy, dxy), sx, sy);
+    LJPairGeom g;
+    g.r2 = __fadd_rn(__fadd_rn(sx, sy), __fmul_rn(dz, dz));
+    g.vx = dx;
+    g.vy = dy;
+    g.vz = dz;
+    g.vr2 = g.r2;
+    if (QBVH_LJ_IMAGE_VALUE && (nx != 0.f || ny != 0.f || nz != 0.f)) {
+        g.vx = mi_value(pj.x, pi.x, nx, L);
+        g.vy = mi_value(pj.y, pi.y, ny, L);
+        g.vz = mi_value(pj.z, pi.z, nz, L);
+        g.vr2 = __fadd_rn(__fadd_rn(__fmul_rn(g.vx, g.vx), __fmul_rn(g.vy, g.vy)), __fmul_rn(g.vz, g.vz));
+    }
+    return g;
 }
 
 // Per-segment (tree) information, written by the build.

@@ -244,21 +244,57 @@ __device__ __forceinline__ void row_store(int *p, int v)
 // hint and does not push the tree out of L2.  (Gathering four entries into
 // one 16-byte store was measured slower: the extra selects and registers cost
 // more than the narrower stores.)
+// Row staging (QBVH_ROW_STAGING = 1): a lane's entries first go to its
+// slot of a per-warp ring in shared memory, one 32-byte sector (8 entries)
+// per lane, slot k of lane l at ring[32 k + l] (conflict-free).  When the
+// count reaches a multiple of 8 the lane writes the completed sector with two
+// 16-byte stores; the partial last sector is written at the end of the
+// particle's walks.  Rows start on 32-byte boundaries (the row capacity is a
+// multiple of 8), so every sector write fills one whole DRAM sector, and the
+// L2 sees one write per 8 entries instead of one per entry.  Measured at
+// N = 2M before staging: the 4-byte row stores took 0.62 of 1.91 ms.
+#ifndef QBVH_ROW_STAGING
+#define QBVH_ROW_STAGING 1
+#endif
+__device__ __forceinline__ void store_sector(int *dst, const int *ring)
+{
+    const int4 lo = make_int4(ring[0], ring[32], ring[64], ring[96]);
+    const int4 hi = make_int4(ring[128], ring[160], ring[192], ring[224]);
+    __stcs(reinterpret_cast<int4 *>(dst), lo);
+    __stcs(reinterpret_cast<int4 *>(dst) + 1, hi);
+}
+
 struct Row {
     int *row;
     int cap;
     int count;
+    int *ring;   // this lane's slot 0 in the warp's staging ring, or nullptr
 
     __device__ __forceinline__ void push(int j)
     {
+        if (ring) {
+            if (count < cap) ring[32 * (count & 7)] = j;
+            ++count;
+            if ((count & 7) == 0 && count <= cap) store_sector(row + count - 8, ring);
+            return;
+        }
         if (count < cap) row_store(row + count, j);
         ++count;
+    }
+
+    // the entries of the last, partial sector (staging only)
+    __device__ __forceinline__ void drain()
+    {
+        if (!ring) return;
+        const int end = min(count, cap);
+        for (int k = end & ~7; k < end; ++k) row_store(row + k, ring[32 * (k & 7)]);
     }
 };
 
 struct Query {
     float xi, yi, zi;     // own position
     int self;             // own sorted index
+    int self_id;          // own original index
     float nLx, nLy, nLz;  // image shift n L
     float px, py, pz;     // image centre fl(x_i + n L)
     float rl2;
@@ -493,10 +529,12 @@ __global__ void query_thread_kernel(const __grid_constant__ QueryArgs a)
         c.yi = me.y;
         c.zi = me.z;
         c.self = s;
+        c.self_id = i_orig;
         Row out;
         out.row = a.rows + (size_t)i_orig * a.cap;
         out.cap = a.cap;
         out.count = 0;
+        out.ring = nullptr;
 
         for (int tb = 0; tb < T; ++tb) {
             const float rl = a.r_list[ta * T + tb];
@@ -611,6 +649,261 @@ __device__ __forceinline__ void bundle_spread(const QueryArgs &a, const Query &c
     }
 }
 
+// ---- 10-bit nodes tested in the integer domain ---------------------------
+// With quantized nodes (Fig. 3b) the walk does not decode the node bounds.
+// Each lane turns the bounding cube of its padded search sphere into the
+// tree's lattice once per image: per axis the cells [ceil((p - rs - R) / h),
+// floor((p + rs - R) / h)], with the divisions rounded outward and clamped to
+// [0, 1023], packed like the node words (x << 20 | y << 10 | z).  A node
+// passes when its packed [lo, hi] overlaps that cube on every axis.  A node
+// box the sphere overlaps overlaps the cube too (the cube contains the
+// sphere, and a node's real box R + [lo, hi] h with integer lo, hi meets
+// [p - rs, p + rs] exactly when lo <= floor(..) and hi >= ceil(..)), so the
+// test never rejects a node the sphere test of Eq. 2 accepts; it accepts a
+// few more (the cube's corners).  All three fields are compared at once: for
+// 10-bit fields a and b, (b | G) - (a & ~G) with G the top bit of every field
+// borrows nothing across fields, its top bits say whether the low 9 bits of b
+// are >= those of a, and (b & ~a) | (~(a ^ b) & t) at the top bits then says
+// b >= a for the whole field.  On the N = 262,144 fluid (CPU walk of the
+// oracle's tree, K = 32) a warp visits 176 nodes against 170 with the FP32
+// sphere test, for about 8 integer operations per node.
+#ifndef QBVH_QCUBE
+#define QBVH_QCUBE 1
+#endif
+#ifndef QBVH_PREFETCH_ROPE
+#define QBVH_PREFETCH_ROPE 0
+#endif
+#ifndef QBVH_PREFETCH_LEFT
+#define QBVH_PREFETCH_LEFT 0
+#endif
+constexpr unsigned kFieldTops = (1u << 29) | (1u << 19) | (1u << 9);
+constexpr unsigned kFieldLows = ~kFieldTops & QBVH_QMASK;
+
+struct LaneCube {
+    unsigned lo, hi;   // packed lattice cells of the search cube
+    unsigned lo_l;     // lo with the fields' top bits cleared
+    unsigned hi_g;     // hi with the fields' top bits set
+    unsigned gm;       // kFieldTops, or 0 for a lane that does not walk this image
+};
+
+__device__ __forceinline__ unsigned cell_lo(float p, float rs, float R, float h)
+{
+    const float v = ceilf(__fdiv_rd(__fsub_rd(__fsub_rd(p, rs), R), h));
+    return (unsigned)fminf(fmaxf(v, 0.f), (float)QBVH_QMAX);
+}
+
+__device__ __forceinline__ unsigned cell_hi(float p, float rs, float R, float h)
+{
+    const float v = floorf(__fdiv_ru(__fsub_ru(__fadd_ru(p, rs), R), h));
+    return (unsigned)fminf(fmaxf(v, 0.f), (float)QBVH_QMAX);
+}
+
+__device__ __forceinline__ LaneCube lane_cube(const Query &c, bool on, const Frame &f, float rs)
+{
+    LaneCube q;
+    q.lo = (cell_lo(c.px, rs, f.rx, f.hx) << 20) | (cell_lo(c.py, rs, f.ry, f.hy) << 10) |
+           cell_lo(c.pz, rs, f.rz, f.hz);
+    q.hi = (cell_hi(c.px, rs, f.rx, f.hx) << 20) | (cell_hi(c.py, rs, f.ry, f.hy) << 10) |
+           cell_hi(c.pz, rs, f.rz, f.hz);
+    q.lo_l = q.lo & kFieldLows;
+    q.hi_g = q.hi | kFieldTops;
+    q.gm = on ? kFieldTops : 0u;
+    return q;
+}
+
+// field-wise b >= a at the fields' top bits, given t = (b | G) - (a & ~G)
+__device__ __forceinline__ unsigned fields_ge(unsigned a, unsigned b, unsigned t)
+{
+    return (b & ~a) | (~(a ^ b) & t);
+}
+
+// node words lo (bit 31: bundle flag) and hi against the lane's cube
+__device__ __forceinline__ bool cube_overlap(unsigned nlo, unsigned nhi, const LaneCube &q)
+{
+    const unsigned x1 = fields_ge(nlo, q.hi, q.hi_g - (nlo & kFieldLows));   // node lo <= cube hi
+    const unsigned x2 = fields_ge(q.lo, nhi, (nhi | kFieldTops) - q.lo_l);   // cube lo <= node hi
+    return (x1 & x2 & q.gm) == kFieldTops;
+}
+
+// ---- bundles filtered against the warp's box of search centres -------------
+// At a bundle every lane first loads one of its (at most 32) leaves and
+// tests it against the box of the warp's image centres grown by the search
+// radius: the distance from the leaf to that box, rounded down, against the
+// rounded-up r_search^2.  If some lane's exact test accepts the leaf, its
+// centre lies in the box and the leaf within the padded radius of it (the
+// conservativeness argument in the header comment), so the leaf survives.
+// Survivors are packed into per-warp shared memory (x, y, z and original
+// index as separate arrays, so that two survivors load as one f32x2 pair),
+// and only they are tested exactly.  On the N = 262,144 fluid (K = 32) a warp
+// tests 517 survivors instead of 1,333 bundle leaves; the union of its 32
+// spheres holds 439 particles (CPU walk of the oracle's tree).
+#ifndef QBVH_PREFILTER
+#define QBVH_PREFILTER 1
+#endif
+#ifndef QBVH_FILTER_SPREAD
+#define QBVH_FILTER_SPREAD 1
+#endif
+#ifndef QBVH_FILTER_SPREAD_MAX
+#define QBVH_FILTER_SPREAD_MAX 16
+#endif
+#ifndef QBVH_SPREAD_COST
+#define QBVH_SPREAD_COST 25
+#endif
+#ifndef QBVH_LOOP_COST
+#define QBVH_LOOP_COST 14
+#endif
+struct BundleStage {
+    float4 blo, bhi;      // the warp's box of image centres (x, y, z)
+    float x[32], y[32], z[32];
+    int id[32];           // original indices of the survivors
+    int owner[32];        // overlapping lanes, in lane order (spread)
+    int ring[8 * 32];     // row staging: slot k of lane l at ring[32 k + l]
+};
+
+// Box of the image centres fl(x_i + n L) of the lanes that walk this image.
+// Positions are in [0, L), so their bit patterns order like the values once
+// -0 is folded into +0; fl(x + n L) is monotone in x, so shifting the
+// unshifted box's corners gives the box of the shifted centres.
+__device__ __forceinline__ void packet_box(const Query &c, bool on, BundleStage *st)
+{
+    const unsigned bx = __float_as_uint(c.xi + 0.f), by = __float_as_uint(c.yi + 0.f),
+                   bz = __float_as_uint(c.zi + 0.f);
+    const float lx = __uint_as_float(__reduce_min_sync(FULL, on ? bx : 0xFFFFFFFFu));
+    const float ly = __uint_as_float(__reduce_min_sync(FULL, on ? by : 0xFFFFFFFFu));
+    const float lz = __uint_as_float(__reduce_min_sync(FULL, on ? bz : 0xFFFFFFFFu));
+    const float hx = __uint_as_float(__reduce_max_sync(FULL, on ? bx : 0u));
+    const float hy = __uint_as_float(__reduce_max_sync(FULL, on ? by : 0u));
+    const float hz = __uint_as_float(__reduce_max_sync(FULL, on ? bz : 0u));
+    if ((threadIdx.x & 31) == 0) {
+        st->blo = make_float4(__fadd_rn(lx, c.nLx), __fadd_rn(ly, c.nLy), __fadd_rn(lz, c.nLz), 0.f);
+        st->bhi = make_float4(__fadd_rn(hx, c.nLx), __fadd_rn(hy, c.nLy), __fadd_rn(hz, c.nLz), 0.f);
+    }
+    __syncwarp();
+}
+
+// Every lane tests every survivor (one particle per lane), two per step: the
+// differences and squares as packed f32x2 pairs, the two sums as scalar adds
+// -- the same operations in the same order as exact_d2.  (ptxas contracts a
+// packed mul.rn.f32x2 feeding a packed add.rn.f32x2 into one fused
+// multiply-add, which changes the rounding of d2: measured on GB300, 8 rows
+// of the N = 2M list differed at d = r_list.  Scalar add.rn is not contracted.)
+template <bool SHIFT, bool SELF>
+__device__ __forceinline__ void survivors_loop(const Query &c, Row &out, int s, bool on, const BundleStage *st)
+{
+    const f32x2 xi2 = f2_pack(c.xi, c.xi), yi2 = f2_pack(c.yi, c.yi), zi2 = f2_pack(c.zi, c.zi);
+    int t = 0;
+    for (; t + 1 < s; t += 2) {
+        const f32x2 X = *reinterpret_cast<const f32x2 *>(st->x + t);
+        const f32x2 Y = *reinterpret_cast<const f32x2 *>(st->y + t);
+        const f32x2 Z = *reinterpret_cast<const f32x2 *>(st->z + t);
+        const int2 id = *reinterpret_cast<const int2 *>(st->id + t);
+        f32x2 dx = f2_sub(X, xi2), dy = f2_sub(Y, yi2), dz = f2_sub(Z, zi2);
+        if (SHIFT) {
+            dx = f2_sub(dx, f2_pack(c.nLx, c.nLx));
+            dy = f2_sub(dy, f2_pack(c.nLy, c.nLy));
+            dz = f2_sub(dz, f2_pack(c.nLz, c.nLz));
+        }
+        float sx0, sx1, sy0, sy1, sz0, sz1;
+        f2_unpack(f2_mul(dx, dx), sx0, sx1);
+        f2_unpack(f2_mul(dy, dy), sy0, sy1);
+        f2_unpack(f2_mul(dz, dz), sz0, sz1);
+        const float d0 = __fadd_rn(__fadd_rn(sx0, sy0), sz0);
+        const float d1 = __fadd_rn(__fadd_rn(sx1, sy1), sz1);
+        if (on && d0 < c.rl2 && (!SELF || id.x != c.self_id)) out.push(id.x);
+        if (on && d1 < c.rl2 && (!SELF || id.y != c.self_id)) out.push(id.y);
+    }
+    if (t < s) {
+        const float4 q = make_float4(st->x[t], st->y[t], st->z[t], 0.f);
+        const int id = st->id[t];
+        if (on && exact_d2<SHIFT>(c, q) < c.rl2 && (!SELF || id != c.self_id)) out.push(id);
+    }
+}
+
+// Survivors spread over the warp when few lanes overlap the bundle: the s
+// survivors occupy s lanes of each of kk = 32 / width slots (width 32, 16 or
+// 8 lanes), and each trip serves kk overlapping particles, whose centre,
+// index and count come by shuffle.  A particle's accepted survivors are
+// packed in survivor order, so the row is the same as with the loop above.
+template <bool SHIFT, bool SELF>
+__device__ __forceinline__ void survivors_spread(const QueryArgs &a, const Query &c, Row &out, int s, int m, int wsh,
+                                                 unsigned hm, const BundleStage *st)
+{
+    const int lane = threadIdx.x & 31;
+    const int kk = 32 >> wsh;                       // particles per trip
+    const int slot = lane >> wsh;
+    const int t = lane & ((1 << wsh) - 1);
+    const bool tv = t < s;
+    const int tt = tv ? t : 0;
+    const float4 q = make_float4(st->x[tt], st->y[tt], st->z[tt], 0.f);
+    const int id = st->id[tt];
+    const unsigned wmask = wsh == 5 ? FULL : ((1u << (1 << wsh)) - 1u);
+    const unsigned smask = wmask << (slot << wsh);  // lanes of my slot
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    const int my_rank = ((hm >> lane) & 1u) ? __popc(hm & lt) : -1;
+    for (int base = 0; base < m; base += kk) {
+        const int oi = base + slot;
+        const int owner = oi < m ? st->owner[oi] : -1;
+        const int src = owner < 0 ? lane : owner;
+        Query u = c;
+        u.xi = __shfl_sync(FULL, c.xi, src);
+        u.yi = __shfl_sync(FULL, c.yi, src);
+        u.zi = __shfl_sync(FULL, c.zi, src);
+        const int ocount = __shfl_sync(FULL, out.count, src);
+        const int oid = __shfl_sync(FULL, c.self_id, src);
+        const bool acc = owner >= 0 && tv && exact_d2<SHIFT>(u, q) < c.rl2 && (!SELF || id != oid);
+        const unsigned mb = __ballot_sync(FULL, acc);
+        if (acc) {
+            const int pos = ocount + __popc(mb & smask & lt);
+            if (pos < out.cap) row_store(a.rows + (size_t)oid * out.cap + pos, id);
+        }
+        const int sl = my_rank - base;
+        if (sl >= 0 && sl < kk) out.count += __popc(mb & (wmask << (sl << wsh)));
+    }
+}
+
+// A bundle of cnt <= 32 leaves starting at `first`, overlapped by the lanes
+// in hm (warp-uniform).  Every lane of the warp calls this together.
+template <bool SHIFT, bool SELF>
+__device__ __forceinline__ void bundle_filtered(const QueryArgs &a, const Query &c, Row &out, int first, int cnt,
+                                                unsigned hm, bool on, float rs2, BundleStage *st)
+{
+    const int lane = threadIdx.x & 31;
+    const bool v = lane < cnt;
+    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (v) q = tree_ld(a.leaves + first + lane);
+    const float4 lo = st->blo, hi = st->bhi;
+    const float gx = fmaxf(fmaxf(__fsub_rd(lo.x, q.x), __fsub_rd(q.x, hi.x)), 0.f);
+    const float gy = fmaxf(fmaxf(__fsub_rd(lo.y, q.y), __fsub_rd(q.y, hi.y)), 0.f);
+    const float gz = fmaxf(fmaxf(__fsub_rd(lo.z, q.z), __fsub_rd(q.z, hi.z)), 0.f);
+    const float g2 = __fmaf_rd(gx, gx, __fmaf_rd(gy, gy, __fmul_rd(gz, gz)));
+    const bool surv = v && g2 <= rs2;
+    const unsigned S = __ballot_sync(FULL, surv);
+    if (S == 0u) return;
+    const int s = __popc(S);
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    if (surv) {
+        const int r = __popc(S & lt);
+        st->x[r] = q.x;
+        st->y[r] = q.y;
+        st->z[r] = q.z;
+        st->id[r] = __float_as_int(q.w) & 0x7FFFFFFF;
+    }
+    // spread when it takes fewer instructions than the loop (about 25 + 3 kk
+    // per trip against 14 per survivor step)
+    const int m = __popc(hm);
+    const int wsh = s <= 8 ? 3 : (s <= 16 ? 4 : 5);
+    const int kk = 32 >> wsh;
+    const bool spread = QBVH_FILTER_SPREAD && !QBVH_ROW_STAGING && m <= QBVH_FILTER_SPREAD_MAX &&
+                        (QBVH_SPREAD_COST + 3 * kk) * ((m + kk - 1) / kk) < QBVH_LOOP_COST * s;
+    if (spread && ((hm >> lane) & 1u)) st->owner[__popc(hm & lt)] = lane;
+    __syncwarp();
+    if (spread) survivors_spread<SHIFT, SELF>(a, c, out, s, m, wsh, hm, st);
+    else survivors_loop<SHIFT, SELF>(c, out, s, on, st);
+    __syncwarp();   // the next bundle rewrites the stage
+}
+
 // bundle leaves tested two per step (two loads in flight; measured 2.25 ->
 // 2.20 ms at N = 2M) or one per step
 #ifndef QBVH_LEAF_PAIRS
@@ -648,9 +941,24 @@ __device__ __forceinline__ void bundle_loop(const QueryArgs &a, const Query &c, 
 template <bool CAND, int FMT, bool SHIFT, int W, bool F64>
 __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Row &out, const SegInfo &g,
                                           const Frame &f, int root, int last, bool on, float rs2, int wsub,
-                                          unsigned same)
+                                          unsigned same, BundleStage *st = nullptr, float rs = 0.f)
 {
+    // bundles filtered against the warp's box (one particle per lane, exact lists of FP32 data)
+    constexpr bool FILTER = QBVH_PREFILTER && W == 1 && !CAND && !F64;
+    // 10-bit nodes tested in the integer domain on the same walks
+    constexpr bool QCUBE = FILTER && FMT == 0 && QBVH_QCUBE;
+    if (FILTER) packet_box(c, on, st);
+    LaneCube cube;
+    if (QCUBE) cube = lane_cube(c, on, f, rs);
     const float lrs2 = on ? rs2 : -1.f;   // a negative squared radius overlaps nothing
+    // node words loaded ahead: the rope target before a bundle's leaves are
+    // tested, and the left child (the next node when a lane overlaps) while
+    // the node itself is tested, so that the walk's dependent loads overlap
+    // other work
+    constexpr bool PREF_ROPE = FILTER && QBVH_PREFETCH_ROPE;
+    constexpr bool PREF_LEFT = FILTER && FMT == 0 && QBVH_PREFETCH_LEFT;
+    Raw ahead;
+    bool have = false;
     int node = root;
     int budget = 2 * g.count;
     while (node != QBVH_END) {
@@ -659,8 +967,22 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
             break;
         }
         if (node >= 0) {
-            const Node nd = decode<FMT>(load_raw<FMT>(a, node), f);
-            const bool hit = overlap(c.px, c.py, c.pz, nd, lrs2);
+            const Raw w = (PREF_ROPE || PREF_LEFT) && have ? ahead : load_raw<FMT>(a, node);
+            have = false;
+            Node nd;
+            bool hit;
+            if (QCUBE) {
+                hit = cube_overlap((unsigned)w.q.x, (unsigned)w.q.y, cube);
+                nd.left = w.q.z;
+                nd.rope = w.q.w;
+                nd.bundle = w.q.x < 0;
+            } else {
+                nd = decode<FMT>(w, f);
+                hit = overlap(c.px, c.py, c.pz, nd, lrs2);
+            }
+            Raw wl;
+            const bool pre_left = PREF_LEFT && !nd.bundle && nd.left >= 0 && !bad_node(nd.left, g, last);
+            if (pre_left) wl = load_raw<FMT>(a, nd.left);
             const unsigned hm = __ballot_sync(FULL, hit);
             if (hm) {
                 if (nd.bundle) {
@@ -669,12 +991,19 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                         atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
                         l = nd.left - 1;
                     }
+                    if (PREF_ROPE && nd.rope >= 0 && !bad_node(nd.rope, g, last)) {
+                        ahead = load_raw<FMT>(a, nd.rope);
+                        have = true;
+                    }
                     int j = nd.left;
                     // only a bundle holding one of the warp's own particles can
                     // hand a lane its own leaf, and only under the zero image
                     const bool self_here =
                         !SHIFT && __any_sync(FULL, (unsigned)(c.self - j) <= (unsigned)(l - j));
-                    if (W == 1 && !CAND && l - j < 32 && __popc(hm) <= QBVH_SPREAD_MAX) {
+                    if (FILTER && l - j < 32) {
+                        if (self_here) bundle_filtered<SHIFT, true>(a, c, out, j, l - j + 1, hm, on, rs2, st);
+                        else bundle_filtered<SHIFT, false>(a, c, out, j, l - j + 1, hm, on, rs2, st);
+                    } else if (W == 1 && !CAND && l - j < 32 && __popc(hm) <= QBVH_SPREAD_MAX) {
                         if (self_here) bundle_spread<SHIFT, F64, true>(a, c, out, j, l - j + 1, hm);
                         else bundle_spread<SHIFT, F64, false>(a, c, out, j, l - j + 1, hm);
                     } else if (W == 1) {
@@ -697,6 +1026,10 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                     node = nd.rope;
                 } else {
                     node = nd.left;
+                    if (pre_left) {
+                        ahead = wl;
+                        have = true;
+                    }
                 }
             } else {
                 node = nd.rope;
@@ -799,10 +1132,12 @@ __device__ __forceinline__ void sparse_walks(const QueryArgs &a)
             c.yi = me.y;
             c.zi = me.z;
             c.self = s;
+            c.self_id = i_orig;
             Row out;
             out.row = a.rows + (size_t)i_orig * a.cap;
             out.cap = a.cap;
             out.count = 0;
+            out.ring = nullptr;
             for (int tb = 0; tb < T; ++tb) {
                 if (!(a.r_list[ta * T + tb] > 0.f)) continue;
                 const SegInfo g = a.seg[tb];
@@ -882,10 +1217,17 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
     c.yi = me.y;
     c.zi = me.z;
     c.self = s;
+    c.self_id = i_orig;
     Row out;
     out.row = a.rows + (size_t)i_orig * a.cap;
     out.cap = a.cap;
     out.count = (PHASE == 1 && active) ? a.counts[i_orig] : 0;
+    constexpr bool STAGE = QBVH_PREFILTER && W == 1 && !CAND && !F64;
+    __shared__ BundleStage stage[STAGE ? 256 / 32 : 1];
+    BundleStage *st = STAGE ? &stage[threadIdx.x >> 5] : nullptr;
+    // row staging on the filtered walks (every push of those walks goes through it)
+    constexpr bool RING = STAGE && QBVH_ROW_STAGING && PHASE == 2;
+    out.ring = RING ? st->ring + lane : nullptr;
     bool walked = PHASE != 1;
     bool elsewhere = false;   // particle of a sparse tree: walked by the leading blocks
     const int T = ONE ? 1 : a.n_types;
@@ -915,13 +1257,14 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
                 c.pair = ta * T + tb;
             }
             const float rs2 = a.rs2[ta * T + tb];
+            const float rs = a.rs[ta * T + tb];
             const Frame f = frame_of(g);
             const int root = g.count >= 2 ? g.start : ~g.start;
             const int last = g.start + g.count - 1;
             if (PHASE == 0) {
                 // zero image: the walk's own root test decides whether it is empty
                 set_image(c, 13, L);
-                warp_walk<CAND, FMT, false, W, F64>(a, c, out, g, f, root, last, part, rs2, wsub, same);
+                warp_walk<CAND, FMT, false, W, F64>(a, c, out, g, f, root, last, part, rs2, wsub, same, st, rs);
                 continue;
             }
             unsigned mine = part ? image_mask(me.x, me.y, me.z, L, g, rs2) : 0u;
@@ -934,13 +1277,14 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
                 set_image(c, img, L);
                 const bool on = (mine >> img) & 1u;
                 if (PHASE == 2 && img == 13)
-                    warp_walk<CAND, FMT, false, W, F64>(a, c, out, g, f, root, last, on, rs2, wsub, same);
+                    warp_walk<CAND, FMT, false, W, F64>(a, c, out, g, f, root, last, on, rs2, wsub, same, st, rs);
                 else
-                    warp_walk<CAND, FMT, true, W, F64>(a, c, out, g, f, root, last, on, rs2, wsub, same);
+                    warp_walk<CAND, FMT, true, W, F64>(a, c, out, g, f, root, last, on, rs2, wsub, same, st, rs);
             }
         }
     }
     if (!walked) return;   // phase 1, no image to add for this warp: counts stay
+    if (RING && active && !elsewhere) out.drain();
     if (active && wsub == 0 && !elsewhere) {
         // the row index again (not kept live across the walk)
         int io = __float_as_int(__ldg(a.leaves + s).w) & 0x7FFFFFFF;
