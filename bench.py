@@ -289,6 +289,35 @@ def run_ours(args):
     t_step = t_build + t_query + t_lj
     total_ms = max_over_ranks(float(t_step.sum()))
 
+    # build and query under each node format (the tuned options otherwise):
+    # the paper's 10-bit quantized nodes (Fig. 3b) and FP32 nodes (Fig. 3a)
+    node_formats = {}
+    fmt_now = nl.get_option(_lib.QBVH_OPT_NODE_FORMAT)
+    for fmt, name in ((0, "quantized_10bit_16B"), (1, "fp32_32B")):
+        nl.set_option(_lib.QBVH_OPT_NODE_FORMAT, fmt)
+        for _ in range(3):
+            step(pos4)
+        tb, tq = [], []
+        for k in range(max(5, min(args.steps, 20))):
+            flush.fill_(float(k))
+            f0, f1, f2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            f0.record(stream)
+            nl.build(pos4, s.L)
+            f1.record(stream)
+            nl.query_async(s.r_list, CAP)
+            f2.record(stream)
+            f2.synchronize()
+            rc_q, _ = nl.query_status()
+            if rc_q != 0:
+                raise RuntimeError(f"query failed: {_lib.QBVHError(rc_q)}")
+            tb.append(f0.elapsed_time(f1))
+            tq.append(f1.elapsed_time(f2))
+        node_formats[name] = {"build_ms": float(np.median(tb)), "query_ms": float(np.median(tq)),
+                              "nlist_particles_per_s": n / ((float(np.median(tb)) + float(np.median(tq))) * 1e-3)}
+    nl.set_option(_lib.QBVH_OPT_NODE_FORMAT, fmt_now)
+    step(pos4)
+    torch.cuda.synchronize()
+
     # end-to-end through the public API with host buffers: every step copies
     # its positions host -> device and its forces and energy device -> host
     # inside the timed region.  The copies run on a second stream with double
@@ -386,6 +415,7 @@ def run_ours(args):
             },
             "breakdown_ms": {"build": float(t_build.mean()), "query": float(t_query.mean()),
                              "lj": float(t_lj.mean())},
+            "node_formats": node_formats,
             "nlist_particles_per_s": n / (float((t_build + t_query).mean()) * 1e-3),
             "roofline": {
                 "kernel": "query_kernel (traversal + exact leaf test + list write)",
@@ -657,7 +687,7 @@ def run_configs(args, local, hbm, bench_ms, bench_nbrs, batched, options):
                 nl.query(q0.r_list, cap=cap)
 
             # a small autotune per configuration, from the bench step's choice
-            space = {_lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8, 4, 1], _lib.QBVH_OPT_BUNDLE: [16, 32],
+            space = {_lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8, 4, 1], _lib.QBVH_OPT_BUNDLE: [16, 32, 64],
                      _lib.QBVH_OPT_NODE_FORMAT: [1, 0], _lib.QBVH_OPT_QUERY_BLOCK: [256, 128, 64]}
             if q0.n_types > 1 and np.all(np.asarray(q0.r_list) == np.asarray(q0.r_list).flat[0]):
                 # one radius for every type pair: one tree per system is an option
@@ -822,8 +852,9 @@ def cpu_baseline(s, samples=1):
         t.append(time.perf_counter() - t0)
     tm = float(np.median(t))
     return {"value": s.n / tm, "unit": "particles/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{samples} full step(s) of the N={s.n} workload: cell-list build+query (OpenMP) "
-                      f"+ FP64 LJ energy/forces (1 thread); {tm:.2f} s per step"}
+            "sample": f"{samples} full step(s) of the N={s.n} workload: cell-list build+query on "
+                      f"{oracle.num_threads()} OpenMP threads, then the FP64 LJ energy/forces single-threaded "
+                      f"(the oracle's LJ has no parallel loop); {tm:.2f} s per step"}
 
 
 def reference_sample_n(steps: int, warmup: int) -> int:

@@ -81,7 +81,7 @@ int qbvh_destroy(qbvh_handle h);
 /* ---- tuning options (qbvh_set_option) ---------------------------------- */
 /* Subtree collapse (Sec. 2.3, final paragraph): internal nodes with at most K
  * leaves are traversed by testing their leaves directly.  K = 1 keeps the
- * paper's one-particle leaves.  Values 1..32, default 16.  Takes effect at
+ * paper's one-particle leaves.  Values 1..64, default 16.  Takes effect at
  * the next build. */
 #define QBVH_OPT_BUNDLE 1
 /* Threads per block of the traversal kernel: 32..256, multiple of 32,

@@ -23,7 +23,7 @@ from . import _lib
 __all__ = ["OPTION_SPACE", "OPTIONAL_SPACE", "DEFAULTS", "tune", "time_step", "option_names"]
 
 OPTION_SPACE = {
-    _lib.QBVH_OPT_BUNDLE: [4, 8, 16, 32],
+    _lib.QBVH_OPT_BUNDLE: [8, 16, 32, 64],
     _lib.QBVH_OPT_NODE_FORMAT: [0, 1],
     _lib.QBVH_OPT_TRAVERSAL: [1, 0],
     _lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8, 4, 1],

@@ -583,7 +583,7 @@ int qbvh_set_option(qbvh_handle h, int option, int value)
     if (!h) return QBVH_ERR_INVALID_ARG;
     switch (option) {
     case QBVH_OPT_BUNDLE:
-        if (value < 1 || value > 32) return QBVH_ERR_INVALID_ARG;
+        if (value < 1 || value > 64) return QBVH_ERR_INVALID_ARG;
         h->bundle_k = value;
         return QBVH_OK;
     case QBVH_OPT_QUERY_BLOCK:

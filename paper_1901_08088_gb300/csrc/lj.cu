@@ -26,15 +26,11 @@ constexpr int kLJBlock = 128;
 #endif
 constexpr int kLJParticles = QBVH_LJ_PARTICLES;   // particles per block, taken in rounds of kLJBlock / TPP
 
-// register cap (0: none); caps of 10 and 12 blocks of 128 threads spill and
-// gain nothing measurable
-#ifndef QBVH_LJ_MIN_BLOCKS
-#define QBVH_LJ_MIN_BLOCKS 0
-#endif
-#if QBVH_LJ_MIN_BLOCKS > 0
-#define QBVH_LJ_BOUNDS __launch_bounds__(kLJBlock, QBVH_LJ_MIN_BLOCKS)
-#else
-#define QBVH_LJ_BOUNDS __launch_bounds__(kLJBlock)
+// Register cap of the one-type pass: 9 blocks of 128 threads (56 registers)
+// keep it free of spills and measured 0.683 -> 0.668 ms at N = 2M; the
+// passes with several types spill under that cap and keep the default.
+#ifndef QBVH_LJ_MIN_BLOCKS_ONE
+#define QBVH_LJ_MIN_BLOCKS_ONE 9
 #endif
 // row entries per load: 4 (16 bytes; 2 measured 0.74 -> 0.83 ms)
 #ifndef QBVH_LJ_VEC
@@ -43,7 +39,8 @@ constexpr int kLJParticles = QBVH_LJ_PARTICLES;   // particles per block, taken 
 // TPP lanes share one particle: lane r of the group takes row entries
 // r, r + TPP, ..., so that a group reads its row in contiguous chunks.
 template <int T, int TPP>
-__global__ void QBVH_LJ_BOUNDS lj_forward_kernel(const __grid_constant__ LJArgs a)
+__global__ void __launch_bounds__(kLJBlock, T == 1 ? QBVH_LJ_MIN_BLOCKS_ONE : 1)
+lj_forward_kernel(const __grid_constant__ LJArgs a)
 {
     constexpr int NP = 1 + 2 * T * T;
     __shared__ LJParams s_par[T * T];

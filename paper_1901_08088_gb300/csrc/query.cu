@@ -670,12 +670,6 @@ __device__ __forceinline__ void bundle_spread(const QueryArgs &a, const Query &c
 #ifndef QBVH_QCUBE
 #define QBVH_QCUBE 1
 #endif
-#ifndef QBVH_PREFETCH_ROPE
-#define QBVH_PREFETCH_ROPE 0
-#endif
-#ifndef QBVH_PREFETCH_LEFT
-#define QBVH_PREFETCH_LEFT 0
-#endif
 constexpr unsigned kFieldTops = (1u << 29) | (1u << 19) | (1u << 9);
 constexpr unsigned kFieldLows = ~kFieldTops & QBVH_QMASK;
 
@@ -862,11 +856,11 @@ __device__ __forceinline__ void survivors_spread(const QueryArgs &a, const Query
     }
 }
 
-// A bundle of cnt <= 32 leaves starting at `first`, overlapped by the lanes
-// in hm (warp-uniform).  Every lane of the warp calls this together.
+// A chunk of cnt <= 32 leaves starting at `first` of a bundle overlapped by
+// the lanes in hm (warp-uniform).  Every lane of the warp calls this together.
 template <bool SHIFT, bool SELF>
-__device__ __forceinline__ void bundle_filtered(const QueryArgs &a, const Query &c, Row &out, int first, int cnt,
-                                                unsigned hm, bool on, float rs2, BundleStage *st)
+__device__ __forceinline__ void bundle_chunk(const QueryArgs &a, const Query &c, Row &out, int first, int cnt,
+                                             unsigned hm, bool on, float rs2, BundleStage *st)
 {
     const int lane = threadIdx.x & 31;
     const bool v = lane < cnt;
@@ -902,6 +896,15 @@ __device__ __forceinline__ void bundle_filtered(const QueryArgs &a, const Query 
     if (spread) survivors_spread<SHIFT, SELF>(a, c, out, s, m, wsh, hm, st);
     else survivors_loop<SHIFT, SELF>(c, out, s, on, st);
     __syncwarp();   // the next bundle rewrites the stage
+}
+
+// A bundle of cnt <= 64 leaves, in chunks of 32 (one leaf per lane).
+template <bool SHIFT, bool SELF>
+__device__ __forceinline__ void bundle_filtered(const QueryArgs &a, const Query &c, Row &out, int first, int cnt,
+                                                unsigned hm, bool on, float rs2, BundleStage *st)
+{
+    for (int base = 0; base < cnt; base += 32)
+        bundle_chunk<SHIFT, SELF>(a, c, out, first + base, min(32, cnt - base), hm, on, rs2, st);
 }
 
 // bundle leaves tested two per step (two loads in flight; measured 2.25 ->
@@ -951,14 +954,6 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
     LaneCube cube;
     if (QCUBE) cube = lane_cube(c, on, f, rs);
     const float lrs2 = on ? rs2 : -1.f;   // a negative squared radius overlaps nothing
-    // node words loaded ahead: the rope target before a bundle's leaves are
-    // tested, and the left child (the next node when a lane overlaps) while
-    // the node itself is tested, so that the walk's dependent loads overlap
-    // other work
-    constexpr bool PREF_ROPE = FILTER && QBVH_PREFETCH_ROPE;
-    constexpr bool PREF_LEFT = FILTER && FMT == 0 && QBVH_PREFETCH_LEFT;
-    Raw ahead;
-    bool have = false;
     int node = root;
     int budget = 2 * g.count;
     while (node != QBVH_END) {
@@ -967,8 +962,7 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
             break;
         }
         if (node >= 0) {
-            const Raw w = (PREF_ROPE || PREF_LEFT) && have ? ahead : load_raw<FMT>(a, node);
-            have = false;
+            const Raw w = load_raw<FMT>(a, node);
             Node nd;
             bool hit;
             if (QCUBE) {
@@ -980,9 +974,6 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                 nd = decode<FMT>(w, f);
                 hit = overlap(c.px, c.py, c.pz, nd, lrs2);
             }
-            Raw wl;
-            const bool pre_left = PREF_LEFT && !nd.bundle && nd.left >= 0 && !bad_node(nd.left, g, last);
-            if (pre_left) wl = load_raw<FMT>(a, nd.left);
             const unsigned hm = __ballot_sync(FULL, hit);
             if (hm) {
                 if (nd.bundle) {
@@ -991,16 +982,12 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                         atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
                         l = nd.left - 1;
                     }
-                    if (PREF_ROPE && nd.rope >= 0 && !bad_node(nd.rope, g, last)) {
-                        ahead = load_raw<FMT>(a, nd.rope);
-                        have = true;
-                    }
                     int j = nd.left;
                     // only a bundle holding one of the warp's own particles can
                     // hand a lane its own leaf, and only under the zero image
                     const bool self_here =
                         !SHIFT && __any_sync(FULL, (unsigned)(c.self - j) <= (unsigned)(l - j));
-                    if (FILTER && l - j < 32) {
+                    if (FILTER && l - j < 64) {
                         if (self_here) bundle_filtered<SHIFT, true>(a, c, out, j, l - j + 1, hm, on, rs2, st);
                         else bundle_filtered<SHIFT, false>(a, c, out, j, l - j + 1, hm, on, rs2, st);
                     } else if (W == 1 && !CAND && l - j < 32 && __popc(hm) <= QBVH_SPREAD_MAX) {
@@ -1026,10 +1013,6 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                     node = nd.rope;
                 } else {
                     node = nd.left;
-                    if (pre_left) {
-                        ahead = wl;
-                        have = true;
-                    }
                 }
             } else {
                 node = nd.rope;

@@ -31,7 +31,20 @@ def test_config1_exact_list_equals_bruteforce(cfg1, bundle, block, traversal, no
     nl.close()
 
 
-@pytest.mark.parametrize("bundle", [1, 4])
+@pytest.mark.parametrize("node_format", [0, 1])
+@pytest.mark.parametrize("n", [4096, 12345, 33, 65, 1000])
+@pytest.mark.parametrize("bundle", [33, 48, 64])
+def test_bundles_wider_than_a_warp(bundle, n, node_format):
+    # bundles of more than 32 leaves are filtered 32 leaves at a time
+    L = max(8.0, (n / 0.6) ** (1 / 3))
+    s = _uniform(n, L, 2.5, seed=n + bundle)
+    rg, cg, nl, _ = gpu_list(s, bundle=bundle, node_format=node_format, block=256)
+    ro, co = oracle_list(s, method="brute")
+    assert_same_lists(rg, cg, ro, co)
+    nl.close()
+
+
+@pytest.mark.parametrize("bundle", [1, 4, 64])
 def test_tree_words_equal_oracle(cfg1, bundle):
     import torch
 
