@@ -19,8 +19,9 @@ Contents (C sources compiled with gcc into ``_oracle.so``):
   (Sec. 2.2): brute force and 27-cell list with one pinned FP64 decision
   expression.
 * ``cand_ref.c``  -- candidate lists of Alg. 1 without the exact leaf filter
-  (Sec. 2.3): every leaf whose quantized box the padded sphere overlaps, under
-  every periodic image whose sphere overlaps the tree's root box; brute force.
+  (Sec. 2.3): every leaf whose box (10-bit or 21-bit quantized, or the FP32
+  point) the padded sphere overlaps, under every periodic image whose sphere
+  overlaps the tree's root box; brute force.
 
 Pins: every function here is checked by ``tests/test_oracle_*.py`` against
 closed forms, brute force, golden hand-derived fixtures and invariants.
@@ -90,9 +91,13 @@ def lib():
             L.or_quantize_box.restype = None
             L.or_dequantize.argtypes = [P, P, P, P, P, P]
             L.or_dequantize.restype = None
+            L.or_quantize_box_q.argtypes = [P, P, P, P, C.c_long, P, P]
+            L.or_quantize_box_q.restype = None
+            L.or_frame_width.argtypes = [P, P, C.c_long, P]
+            L.or_frame_width.restype = None
             L.or_lj_fp64.argtypes = [i32, P, P, P, f32, i32, P, P, P, i32, P, P, P, P, P, P, P]
             L.or_lj_fp64.restype = i32
-            L.or_candidates.argtypes = [i32, P, P, f32, i32, P, P, P, i32, P, P]
+            L.or_candidates.argtypes = [i32, P, P, f32, i32, P, P, P, i32, i32, P, P]
             L.or_candidates.restype = i32
             _lib = L
     return _lib
@@ -134,9 +139,10 @@ def nlist(pos, L, r_list, types=None, n_types=1, cap=256, method="cell"):
     return rows, counts
 
 
-def candidates(pos, L, r_list, types=None, n_types=1, cap=256):
-    """Candidate lists of Alg. 1 (no exact leaf filter, 10-bit leaf boxes, one
-    tree per type).  Returns (rows [n,cap] int32 sorted asc, counts [n] int32);
+def candidates(pos, L, r_list, types=None, n_types=1, cap=256, leaf_bits=10):
+    """Candidate lists of Alg. 1 (no exact leaf filter, one tree per type),
+    against leaf boxes quantized to 10 or 21 bits, or the FP32 points
+    (leaf_bits=0).  Returns (rows [n,cap] int32 sorted asc, counts [n] int32);
     an index appears once per periodic image that lists it."""
     pos = _c(pos, np.float32).reshape(-1, 3)
     n = pos.shape[0]
@@ -147,7 +153,7 @@ def candidates(pos, L, r_list, types=None, n_types=1, cap=256):
     rows = np.full((n, cap), -1, np.int32)
     counts = np.zeros(n, np.int32)
     rc = lib().or_candidates(n, _p(pos), _p(types), float(L32), n_types, _p(rl), _p(tree["root"]),
-                             _p(tree["frame"]), cap, _p(rows), _p(counts))
+                             _p(tree["frame"]), int(leaf_bits), cap, _p(rows), _p(counts))
     if rc != 0:
         raise RuntimeError(f"oracle candidates failed ({rc})")
     return rows, counts
@@ -243,12 +249,23 @@ def lbvh_topology(pos, seg, Lseg):
     return t
 
 
-def quantize_box(lo, hi, R_lo, h):
+def quantize_box(lo, hi, R_lo, h, bits=10):
+    """Outward quantization of a box onto the bin edges 0..2^bits - 1."""
     a = [_c(v, np.float32) for v in (lo, hi, R_lo, h)]
     qlo = np.zeros(3, np.uint32)
     qhi = np.zeros(3, np.uint32)
-    lib().or_quantize_box(*[_p(v) for v in a], _p(qlo), _p(qhi))
+    if bits == 10:
+        lib().or_quantize_box(*[_p(v) for v in a], _p(qlo), _p(qhi))
+    else:
+        lib().or_quantize_box_q(*[_p(v) for v in a], (1 << bits) - 1, _p(qlo), _p(qhi))
     return qlo, qhi
+
+
+def frame_width(R_lo, R_hi, bits):
+    """Bin width per axis of a root box with 2^bits - 1 bins (rounded up)."""
+    h = np.zeros(3, np.float32)
+    lib().or_frame_width(_p(_c(R_lo, np.float32)), _p(_c(R_hi, np.float32)), (1 << bits) - 1, _p(h))
+    return h
 
 
 def dequantize(qlo, qhi, R_lo, h):

@@ -3,8 +3,10 @@
  *
  * Candidate lists of Alg. 1 as written, without the exact leaf filter: the
  * paper lists every particle whose quantized leaf box the search sphere
- * overlaps and leaves false positives to a later stage (Sec. 2.3).  Written
- * here as the plain set the rope walk reaches, by brute force over all leaves:
+ * overlaps and leaves false positives to a later stage (Sec. 2.3); how many
+ * depends on the precision of the leaf boxes (10-bit, 21-bit, or the FP32
+ * point, Sec. 2.2).  Written here as the plain set the rope walk reaches, by
+ * brute force over all leaves:
  *
  *   for particle i of type a, every tree b (the particles of type b) with
  *   r = r_list[a][b] > 0, and every periodic image n in {-1, 0, 1}^3
@@ -43,8 +45,9 @@
 #include <omp.h>
 #endif
 
-void or_quantize_box(const float *lo, const float *hi, const float *R_lo, const float *h,
-                     uint32_t *qlo, uint32_t *qhi);
+void or_quantize_box_q(const float *lo, const float *hi, const float *R_lo, const float *h, long qmax,
+                       uint32_t *qlo, uint32_t *qhi);
+void or_frame_width(const float *R_lo, const float *R_hi, long qmax, float *h);
 void or_dequantize(const uint32_t *qlo, const uint32_t *qhi, const float *R_lo, const float *h,
                    float *lo, float *hi);
 
@@ -96,15 +99,20 @@ static int cmp_int(const void *a, const void *b)
 /*
  * pos [n][3] float32 in [0, L), types [n] in [0, nt), rl [nt][nt] list radii,
  * root [nt][6] (lo xyz, hi xyz) and frame [nt][6] (R_lo xyz, h xyz) of each
- * type's tree as the LBVH build makes them.
+ * type's tree as the LBVH build makes them (the 10-bit frame).
+ * leaf_bits: precision of the leaf boxes the candidates are tested against:
+ *   10 = 10-bit quantized (Fig. 3b, the frame given), 21 = 21-bit quantized
+ *   (bin width from the root box with 2^21 - 1 bins, or_frame_width), 0 = the
+ *   FP32 point itself (the leaf of an uncompressed tree, Fig. 3a).
  * rows [n][cap] out (sorted ascending, an index repeated once per image that
  * lists it), counts [n] out (full count even past cap).
  * Returns 0, or -1 on bad input.
  */
 int or_candidates(int n, const float *pos, const int *types, float L, int nt, const float *rl,
-                  const float *root, const float *frame, int cap, int *rows, int *counts)
+                  const float *root, const float *frame, int leaf_bits, int cap, int *rows, int *counts)
 {
     if (n < 0 || nt < 1 || cap < 1 || !(L > 0.f)) return -1;
+    if (leaf_bits != 0 && leaf_bits != 10 && leaf_bits != 21) return -1;
     for (int i = 0; i < n; ++i)
         if (types[i] < 0 || types[i] >= nt) return -1;
     /* decoded leaf boxes */
@@ -119,10 +127,19 @@ int or_candidates(int n, const float *pos, const int *types, float L, int nt, co
     }
     for (int j = 0; j < n; ++j) {
         const float *fr = frame + 6 * types[j];
-        uint32_t qlo[3], qhi[3];
-        or_quantize_box(pos + 3 * (size_t)j, pos + 3 * (size_t)j, fr, fr + 3, qlo, qhi);
-        or_dequantize(qlo, qhi, fr, fr + 3, blo + 3 * (size_t)j, bhi + 3 * (size_t)j);
+        const float *x = pos + 3 * (size_t)j;
         cnt_t[types[j]]++;
+        if (leaf_bits == 0) {
+            for (int d = 0; d < 3; ++d) blo[3 * (size_t)j + d] = bhi[3 * (size_t)j + d] = x[d];
+            continue;
+        }
+        float h[3];
+        const long qmax = leaf_bits == 21 ? (1L << 21) - 1 : 1023;
+        if (leaf_bits == 21) or_frame_width(root + 6 * types[j], root + 6 * types[j] + 3, qmax, h);
+        else for (int d = 0; d < 3; ++d) h[d] = fr[3 + d];
+        uint32_t qlo[3], qhi[3];
+        or_quantize_box_q(x, x, fr, h, qmax, qlo, qhi);
+        or_dequantize(qlo, qhi, fr, h, blo + 3 * (size_t)j, bhi + 3 * (size_t)j);
     }
     /* padded radii and their squares */
     float rs2[64];

@@ -369,21 +369,44 @@ int or_lbvh_topology(int n, const float *pos, const int *seg, int n_seg, const f
     return 0;
 }
 
-/* Quantize one AABB against a frame, exposed for the containment tests. */
-void or_quantize_box(const float *lo, const float *hi, const float *R_lo, const float *h,
-                     uint32_t *qlo, uint32_t *qhi)
+/*
+ * Quantize one AABB against a frame onto the bin edges 0..qmax (qmax = 1023
+ * for the 10-bit words of Fig. 3b, 2^21 - 1 for 21-bit words: the bit width
+ * that trades node size against false positives, Sec. 2.2), lower bound
+ * rounded down and upper bound up as above.
+ */
+void or_quantize_box_q(const float *lo, const float *hi, const float *R_lo, const float *h, long qmax,
+                       uint32_t *qlo, uint32_t *qhi)
 {
     fesetround(FE_DOWNWARD);
     for (int d = 0; d < 3; ++d) {
         long q = (long)floorf(v_div(v_sub(lo[d], R_lo[d]), h[d]));
-        qlo[d] = (uint32_t)(q < 0 ? 0 : (q > 1023 ? 1023 : q));
+        qlo[d] = (uint32_t)(q < 0 ? 0 : (q > qmax ? qmax : q));
     }
     fesetround(FE_UPWARD);
     for (int d = 0; d < 3; ++d) {
         long q = (long)ceilf(v_div(v_sub(hi[d], R_lo[d]), h[d]));
-        qhi[d] = (uint32_t)(q < 0 ? 0 : (q > 1023 ? 1023 : q));
+        qhi[d] = (uint32_t)(q < 0 ? 0 : (q > qmax ? qmax : q));
     }
     fesetround(FE_TONEAREST);
+}
+
+/* The 10-bit case, exposed for the containment tests. */
+void or_quantize_box(const float *lo, const float *hi, const float *R_lo, const float *h,
+                     uint32_t *qlo, uint32_t *qhi)
+{
+    or_quantize_box_q(lo, hi, R_lo, h, 1023, qlo, qhi);
+}
+
+/* Bin width of a frame with qmax bins per axis: (R_hi - R_lo) / qmax rounded
+ * up, at least the smallest normal float (a root of zero width). */
+void or_frame_width(const float *R_lo, const float *R_hi, long qmax, float *h)
+{
+    fesetround(FE_UPWARD);
+    for (int d = 0; d < 3; ++d) h[d] = v_div(v_sub(R_hi[d], R_lo[d]), (float)qmax);
+    fesetround(FE_TONEAREST);
+    for (int d = 0; d < 3; ++d)
+        if (!(h[d] >= FLT_MIN)) h[d] = FLT_MIN;
 }
 
 /*

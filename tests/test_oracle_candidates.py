@@ -35,14 +35,19 @@ def _padded_r2(r, L):
     return float(up(Fraction(float(rs)) ** 2))
 
 
-def _boxes(pos, types, n_types, L):
+def _boxes(pos, types, n_types, L, leaf_bits=10):
     tree = oracle.lbvh_build(pos, types, np.full(n_types, np.float32(L), np.float32))
     lo = np.zeros((len(pos), 3), np.float64)
     hi = np.zeros((len(pos), 3), np.float64)
     for j, p in enumerate(pos):
+        if leaf_bits == 0:   # FP32 leaves: the point itself
+            lo[j] = hi[j] = p
+            continue
         fr = tree["frame"][types[j]]
-        ql, qh = oracle.quantize_box(p, p, fr[:3], fr[3:])
-        a, b = oracle.dequantize(ql, qh, fr[:3], fr[3:])
+        h = fr[3:] if leaf_bits == 10 else oracle.frame_width(tree["root"][types[j], :3],
+                                                              tree["root"][types[j], 3:], leaf_bits)
+        ql, qh = oracle.quantize_box(p, p, fr[:3], h, bits=leaf_bits)
+        a, b = oracle.dequantize(ql, qh, fr[:3], h)
         lo[j], hi[j] = a, b
     return tree["root"].astype(np.float64), lo, hi
 
@@ -52,11 +57,11 @@ def _box_d2(p, lo, hi):
     return (g * g).sum(-1)
 
 
-def _expected(pos, types, n_types, L, rl):
+def _expected(pos, types, n_types, L, rl, leaf_bits=10):
     """FP64 restatement: per (i, j) the images that certainly list j (all
     distances within rs2) and the images that may list it (within rs2 up to a
     relative 1e-6)."""
-    root, lo, hi = _boxes(pos, types, n_types, L)
+    root, lo, hi = _boxes(pos, types, n_types, L, leaf_bits)
     n = len(pos)
     L32 = np.float32(L)
     must = np.zeros((n, n), np.int32)
@@ -92,9 +97,10 @@ def _multiplicity(rows, counts, n):
     return mult
 
 
+@pytest.mark.parametrize("leaf_bits", [10, 21, 0])
 @pytest.mark.parametrize("n,L,r,n_types,seed", [(1500, 15.0, 2.5, 1, 1), (1200, 12.0, 2.0, 2, 2),
                                                 (300, 9.0, 4.4, 1, 3)])
-def test_candidates_between_fp64_bounds(n, L, r, n_types, seed):
+def test_candidates_between_fp64_bounds(n, L, r, n_types, seed, leaf_bits):
     rng = np.random.default_rng(seed)
     pos = rng.uniform(0, L, size=(n, 3)).astype(np.float32)
     pos[pos >= np.float32(L)] = 0
@@ -102,10 +108,10 @@ def test_candidates_between_fp64_bounds(n, L, r, n_types, seed):
     rl = np.full((n_types, n_types), r, np.float32)
     if n_types == 2:
         rl = np.array([[r, r * 1.3], [r * 1.3, r * 0.7]], np.float32)
-    rows, counts = oracle.candidates(pos, L, rl, types, n_types, cap=2048)
+    rows, counts = oracle.candidates(pos, L, rl, types, n_types, cap=2048, leaf_bits=leaf_bits)
     assert counts.max() <= 2048
     mult = _multiplicity(rows, counts, n)
-    must, may = _expected(pos, types, n_types, L, rl)
+    must, may = _expected(pos, types, n_types, L, rl, leaf_bits)
     assert (mult >= must).all(), np.argwhere(mult < must)[:5]
     assert (mult <= may).all(), np.argwhere(mult > may)[:5]
 
@@ -156,3 +162,21 @@ def test_candidates_segregated_types_use_each_trees_root_box():
     assert must.sum() > 0
     assert (mult >= must).all(), np.argwhere(mult < must)[:5]
     assert (mult <= may).all(), np.argwhere(mult > may)[:5]
+
+
+def test_false_positives_shrink_with_the_leaf_precision():
+    # a leaf box contains its point, and the overlap test is monotone in the
+    # box: FP32-point candidates are a subset of the 21-bit ones and of the
+    # 10-bit ones; the 21-bit boxes (bin width L / 2^21) leave almost no false
+    # positives beyond the radius padding, the 10-bit ones a few percent
+    s = workloads.workload("lj_n4096_rho0.6", seed=0)
+    ro, co = oracle.nlist(s.pos, s.L, s.r_list, method="brute")
+    out = {}
+    for bits in (0, 21, 10):
+        rc, cc = oracle.candidates(s.pos, s.L, s.r_list, cap=512, leaf_bits=bits)
+        out[bits] = (oracle.rows_as_sets(rc, cc), cc)
+    for i in range(s.n):
+        assert out[0][0][i] <= out[21][0][i] and out[0][0][i] <= out[10][0][i]
+    fp = {b: (out[b][1] - co).mean() for b in out}
+    assert 0 <= fp[0] <= fp[21] < fp[10]
+    assert fp[21] < 0.002 * co.mean() and fp[10] < 0.05 * co.mean()

@@ -306,3 +306,69 @@ def test_node_and_leaf_words(K):
             assert (tag >> 31) == int(r >= 0)
             # a leaf's rope is always the node starting at the next leaf, or the end
             assert r == END if k == b else (r == k + 1 or r == ~(k + 1))
+
+
+def _exact_width(r_lo, r_hi, bins):
+    """Bin width (r_hi - r_lo) / bins in exact arithmetic, rounded up to FP32."""
+    from fractions import Fraction
+    x = (Fraction(float(r_hi)) - Fraction(float(r_lo))) / bins
+    f = np.float32(float(x))
+    if Fraction(float(f)) < x:
+        f = np.nextafter(f, np.float32(np.inf))
+    return f
+
+
+def test_frame_width_21_bit_is_the_rounded_up_quotient():
+    # 2^21 - 1 bins per axis: the width is the exact quotient rounded up (the
+    # oracle forms the difference and the quotient under round-up in FP32)
+    rng = np.random.default_rng(21)
+    for _ in range(500):
+        R_lo = rng.uniform(0, 100, 3).astype(np.float32)
+        R_hi = (R_lo + (10.0 ** rng.uniform(-2, 2.5, 3))).astype(np.float32)
+        h = oracle.frame_width(R_lo, R_hi, 21)
+        for d in range(3):
+            exact = _exact_width(R_lo[d], R_hi[d], 2 ** 21 - 1)
+            # FP32 round-up of the difference first: never below the exact
+            # quotient, at most two ulps above it
+            assert h[d] >= exact and h[d] <= np.nextafter(np.nextafter(exact, np.float32(np.inf)),
+                                                          np.float32(np.inf))
+    assert (oracle.frame_width(np.zeros(3), np.zeros(3), 21) == np.finfo(np.float32).tiny).all()
+
+
+def test_outward_quantization_21_bit_never_loses_volume_and_is_tight():
+    rng = np.random.default_rng(22)
+    bad = loose = 0
+    for _ in range(3000):
+        R_lo = rng.uniform(-50, 50, 3).astype(np.float32)
+        R_hi = (R_lo + (10.0 ** rng.uniform(-2, 3, 3))).astype(np.float32)
+        h = oracle.frame_width(R_lo, R_hi, 21)
+        a = rng.uniform(R_lo, R_hi).astype(np.float32)
+        b = rng.uniform(R_lo, R_hi).astype(np.float32)
+        lo, hi = np.minimum(a, b), np.maximum(a, b)
+        if rng.random() < 0.2:
+            lo = R_lo.copy()
+        if rng.random() < 0.2:
+            hi = R_hi.copy()
+        qlo, qhi = oracle.quantize_box(lo, hi, R_lo, h, bits=21)
+        assert (qhi <= 2 ** 21 - 1).all() and (qlo <= qhi).all()
+        dlo, dhi = oracle.dequantize(qlo, qhi, R_lo, h)
+        bad += not ((dlo <= lo).all() and (dhi >= hi).all())
+        # within two bins (plus FP32 rounding of the decode) of the box
+        slack = 2 * h.astype(np.float64) + 4 * np.spacing(np.abs(R_hi).astype(np.float32)).astype(np.float64)
+        loose += not ((lo - dlo <= slack).all() and (dhi - hi <= slack).all())
+    assert bad == 0 and loose == 0
+
+
+def test_21_bit_boxes_detect_a_frame_built_for_10_bits():
+    # planted mistake: 21-bit codes decoded with the 10-bit bin width land far
+    # outside the box they came from
+    R_lo = np.zeros(3, np.float32)
+    R_hi = np.full(3, 50.0, np.float32)
+    h21 = oracle.frame_width(R_lo, R_hi, 21)
+    h10 = oracle.frame_width(R_lo, R_hi, 10)
+    lo = np.full(3, 20.0, np.float32)
+    qlo, qhi = oracle.quantize_box(lo, lo, R_lo, h21, bits=21)
+    dlo, dhi = oracle.dequantize(qlo, qhi, R_lo, h10)
+    assert not ((dlo <= lo).all() and (dhi >= lo).all())
+    dlo, dhi = oracle.dequantize(qlo, qhi, R_lo, h21)
+    assert (dlo <= lo).all() and (dhi >= lo).all()
