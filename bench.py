@@ -293,7 +293,7 @@ def run_ours(args):
     # the paper's 10-bit quantized nodes (Fig. 3b) and FP32 nodes (Fig. 3a)
     node_formats = {}
     fmt_now = nl.get_option(_lib.QBVH_OPT_NODE_FORMAT)
-    for fmt, name in ((0, "quantized_10bit_16B"), (1, "fp32_32B")):
+    for fmt, name in ((0, "quantized_10bit_16B"), (1, "fp32_32B"), (2, "quantized_21bit_32B")):
         nl.set_option(_lib.QBVH_OPT_NODE_FORMAT, fmt)
         for _ in range(3):
             step(pos4)
@@ -410,7 +410,8 @@ def run_ours(args):
                 "query_block": nl.get_option(_lib.QBVH_OPT_QUERY_BLOCK),
                 "traversal": ["thread_per_particle", "warp_per_32_particles"][
                     nl.get_option(_lib.QBVH_OPT_TRAVERSAL)],
-                "node_format": ["quantized_10bit_16B", "fp32_32B"][nl.get_option(_lib.QBVH_OPT_NODE_FORMAT)],
+                "node_format": ["quantized_10bit_16B", "fp32_32B", "quantized_21bit_32B"][
+                    nl.get_option(_lib.QBVH_OPT_NODE_FORMAT)],
                 "lj_lanes_per_particle": nl.get_option(_lib.QBVH_OPT_LJ_LANES),
             },
             "breakdown_ms": {"build": float(t_build.mean()), "query": float(t_query.mean()),
@@ -447,6 +448,7 @@ def run_ours(args):
         if not args.no_grid_compare and world == 1 and not args.n:
             out["grid_comparison"] = run_grid_comparison(args, local)
             out["fp64_data"] = run_fp64_comparison(args, local)
+            out["false_positives_per_particle"] = run_false_positives(local)
             out["configs"] = run_configs(args, local, hbm, float((t_build + t_query).mean()), mean_nbrs,
                                          out.get("batched"), {k: nl.get_option(k) for k in autotune.OPTION_SPACE})
         if not args.no_cpu_baseline and world == 1:
@@ -582,6 +584,39 @@ def run_grid_comparison(args, local):
             nl.close()
         res["bvh_speedup_over_grid"] = res["grid_ms"] / res["bvh_ms"]
         out.append(res)
+    return out
+
+
+def run_false_positives(local):
+    """Alg. 1 without the exact leaf test (candidate mode) on the paper's LJ
+    state points (N = 128,000, r_c = 3.0, rho 0.2 and 0.8; Sec. 4.1 counts the
+    false positives of its 10-bit tree): false positives per particle with
+    the leaves tested at each node format's precision -- 10-bit and 21-bit
+    quantized boxes, and the FP32 points (the bit width Sec. 2.2 weighs)."""
+    import torch
+
+    import workloads
+    from paper_1901_08088_gb300 import NeighborList, _lib
+
+    out = {"paper": "about 1.5 and 3.8 false positives per particle at rho 0.2 and 0.8 with 10-bit nodes "
+                    "(Sec. 4.1)"}
+    for rho in (0.2, 0.8):
+        s = workloads.jittered_lattice(128_000, rho, 0.3, seed=1, r_cut=3.0, skin=0.0)
+        pos4 = torch.from_numpy(workloads.pack_float4(s.pos, s.types)).cuda()
+        res = {}
+        for fmt, name in ((0, "quantized_10bit"), (2, "quantized_21bit"), (1, "fp32")):
+            counts = []
+            for cand in (0, 1):
+                nl = NeighborList(local)
+                nl.set_option(_lib.QBVH_OPT_NODE_FORMAT, fmt)
+                nl.set_option(_lib.QBVH_OPT_CANDIDATES, cand)
+                nl.build(pos4, s.L)
+                nl.query(s.r_list, cap=512)
+                counts.append(float(nl.neighbors()[1].double().mean().item()))
+                nl.close()
+            res["true_neighbours"] = counts[0]
+            res[name] = counts[1] - counts[0]
+        out[f"rho_{rho}"] = res
     return out
 
 

@@ -98,8 +98,13 @@ int qbvh_destroy(qbvh_handle h);
  * its own sphere).  Both give the same list.  Takes effect at the next query. */
 #define QBVH_OPT_TRAVERSAL 4
 /* Node storage: 0 (default) = 16-byte nodes with 10-bit quantized bounds
- * (Fig. 3b); 1 = 32-byte nodes with exact FP32 bounds (Fig. 3a).  Both give
- * the same list.  Takes effect at the next build. */
+ * (Fig. 3b); 1 = 32-byte nodes with exact FP32 bounds (Fig. 3a); 2 = 32-byte
+ * nodes with bounds quantized to 21 bits per axis (2^21 - 1 bins on the root
+ * box, the wider bit width Sec. 2.2 weighs against false positives).  All
+ * give the same list; in candidate mode (QBVH_OPT_CANDIDATES) the leaves are
+ * tested at the format's precision (10-bit box, FP32 point, 21-bit box), so
+ * the false positives differ.  qbvh_tree_get returns the 10-bit nodes, which
+ * every build writes.  Takes effect at the next build. */
 #define QBVH_OPT_NODE_FORMAT 5
 /* Lanes that share one particle's row in qbvh_lj_forward: 1, 2, 4, 8, 16 or
  * 32 (default 2).  More lanes read a row in longer contiguous chunks. */

@@ -2,7 +2,8 @@
 
 The paper lets runtime autotuners pick the kernel launch parameters during
 warm-up and then freezes them (Sec. 4).  Here the tuned options are the
-subtree-collapse size, the node format (10-bit quantized or FP32 bounds), the
+subtree-collapse size, the node format (10-bit or 21-bit quantized, or FP32
+bounds: the bit width of the quantization, Sec. 2.2), the
 traversal mapping (thread or warp per particle), the traversal block size and
 the lanes per particle of the LJ pass; where every type pair has the same
 list radius a caller may add one tree per system instead of one per type.
@@ -24,7 +25,7 @@ __all__ = ["OPTION_SPACE", "OPTIONAL_SPACE", "DEFAULTS", "tune", "time_step", "o
 
 OPTION_SPACE = {
     _lib.QBVH_OPT_BUNDLE: [8, 16, 32, 64],
-    _lib.QBVH_OPT_NODE_FORMAT: [0, 1],
+    _lib.QBVH_OPT_NODE_FORMAT: [0, 1, 2],
     _lib.QBVH_OPT_TRAVERSAL: [1, 0],
     _lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8, 4, 1],
     _lib.QBVH_OPT_QUERY_BLOCK: [64, 128, 256],

@@ -61,7 +61,7 @@ struct qbvh_ctx {
     int candidates = 0;
     int traversal = 1;
     int warp_particles = 32;
-    int node_fmt = 0;      // 0: 10-bit quantized nodes (Fig. 3b), 1: FP32 nodes (Fig. 3a)
+    int node_fmt = 0;      // 0: 10-bit quantized nodes (Fig. 3b), 1: FP32 nodes (Fig. 3a), 2: 21-bit nodes
     int lj_tpp = 2;        // lanes per particle in the LJ pass
     int lj_zorder = 1;     // LJ pass walks particles in the tree's Z-order
     int method = 0;        // 0: quantized BVH, 1: uniform grid comparator
@@ -88,7 +88,8 @@ struct qbvh_ctx {
     int max_count = 0;
     float r_list[64];
     // device buffers
-    DevBuf keys[2], vals[2], sort_scratch, nodes, nodes32, leaves, leaf_q, range, child, par_int, par_leaf, visit;
+    DevBuf keys[2], vals[2], sort_scratch, nodes, nodes32, nodes21, leaves, leaf_q, range, child, par_int, par_leaf,
+        visit;
     DevBuf seg, acc, seg_start, frames, sys, sys_off, status;
     DevBuf rows, counts;
     DevBuf cell_start, stype;
@@ -265,6 +266,7 @@ int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *of
     rc = rc ? rc : ensure(h, h->sort_scratch, sort_scratch_bytes(n, passes));
     rc = rc ? rc : ensure(h, h->nodes, nn * sizeof(int4));
     if (h->node_fmt == 1) rc = rc ? rc : ensure(h, h->nodes32, nn * 2 * sizeof(float4));
+    if (h->node_fmt == 2) rc = rc ? rc : ensure(h, h->nodes21, nn * 2 * sizeof(int4));
     rc = rc ? rc : ensure(h, h->leaves, nn * sizeof(float4));
     if (f64) rc = rc ? rc : ensure(h, h->leaves64, nn * 4 * sizeof(double));
     rc = rc ? rc : ensure(h, h->leaf_q, nn * sizeof(uint2));
@@ -312,6 +314,7 @@ int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *of
     a.leaf_q = reinterpret_cast<uint2 *>(h->leaf_q.p);
     a.nodes = reinterpret_cast<int4 *>(h->nodes.p);
     a.nodes32 = h->node_fmt == 1 ? reinterpret_cast<float4 *>(h->nodes32.p) : nullptr;
+    a.nodes21 = h->node_fmt == 2 ? reinterpret_cast<int4 *>(h->nodes21.p) : nullptr;
     a.leaves = reinterpret_cast<float4 *>(h->leaves.p);
     a.status = reinterpret_cast<DevStatus *>(h->status.p);
     a.sort_scratch = reinterpret_cast<unsigned *>(h->sort_scratch.p);
@@ -473,6 +476,7 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
     }
     q.nodes = reinterpret_cast<const int4 *>(h->nodes.p);
     q.nodes32 = reinterpret_cast<const float4 *>(h->nodes32.p);
+    q.nodes21 = reinterpret_cast<const int4 *>(h->nodes21.p);
     q.node_fmt = h->built_fmt;
     q.leaves = reinterpret_cast<const float4 *>(h->leaves.p);
     q.leaf_q = reinterpret_cast<const uint2 *>(h->leaf_q.p);
@@ -567,6 +571,7 @@ int qbvh_destroy(qbvh_handle h)
         DeviceGuard g(h->device);
         cudaDeviceSynchronize();
         DevBuf *all[] = {&h->keys[0], &h->keys[1], &h->vals[0], &h->vals[1], &h->sort_scratch, &h->nodes, &h->nodes32,
+                         &h->nodes21,
                          &h->leaves, &h->leaf_q, &h->range, &h->child, &h->par_int, &h->par_leaf, &h->visit,
                          &h->seg, &h->acc, &h->seg_start, &h->frames, &h->sys, &h->sys_off, &h->status,
                          &h->rows, &h->counts, &h->cell_start, &h->stype, &h->lj_partials, &h->lj_blk_sys, &h->lj_blk_first,
@@ -599,7 +604,7 @@ int qbvh_set_option(qbvh_handle h, int option, int value)
         h->traversal = value;
         return QBVH_OK;
     case QBVH_OPT_NODE_FORMAT:
-        if (value != 0 && value != 1) return QBVH_ERR_INVALID_ARG;
+        if (value < 0 || value > 2) return QBVH_ERR_INVALID_ARG;
         h->node_fmt = value;
         return QBVH_OK;
     case QBVH_OPT_LJ_LANES:

@@ -277,9 +277,13 @@ __global__ void __launch_bounds__(1024) seg_scan_kernel(const BuildArgs a, const
                 // bin width: (R_hi - R_lo) / 1023 rounded up, so 1023 bins cover the root
                 float h = __fdiv_ru(__fsub_ru(hi, lo), (float)QBVH_QMAX);
                 if (!(h >= FLT_MIN)) h = FLT_MIN;
+                // and for the 21-bit node format, 2^21 - 1 bins
+                float h21 = __fdiv_ru(__fsub_ru(hi, lo), (float)QBVH_QMAX21);
+                if (!(h21 >= FLT_MIN)) h21 = FLT_MIN;
                 g.rlo[d] = lo;
                 g.rhi[d] = hi;
                 g.h[d] = h;
+                g.h21[d] = h21;
                 fr[d] = lo;
                 fr[3 + d] = h;
             }
@@ -396,6 +400,40 @@ __device__ __forceinline__ unsigned q_up(float x, float r, float h)
     return (unsigned)v;
 }
 
+// 21-bit fields, three per 64-bit word (x << 42 | y << 21 | z)
+__device__ __forceinline__ unsigned long long pack21(unsigned x, unsigned y, unsigned z)
+{
+    return ((unsigned long long)x << 42) | ((unsigned long long)y << 21) | z;
+}
+
+__device__ __forceinline__ unsigned field21(unsigned long long w, int shift)
+{
+    return (unsigned)(w >> shift) & (unsigned)QBVH_QMAX21;
+}
+
+__device__ __forceinline__ unsigned long long qmin21(unsigned long long a, unsigned long long b)
+{
+    return pack21(min(field21(a, 42), field21(b, 42)), min(field21(a, 21), field21(b, 21)),
+                  min(field21(a, 0), field21(b, 0)));
+}
+
+__device__ __forceinline__ unsigned long long qmax21(unsigned long long a, unsigned long long b)
+{
+    return pack21(max(field21(a, 42), field21(b, 42)), max(field21(a, 21), field21(b, 21)),
+                  max(field21(a, 0), field21(b, 0)));
+}
+
+// the 21-bit box {lo64, hi64} of an FP32 box against tree g
+__device__ __forceinline__ ulonglong2 quantize21(const float3 &lo, const float3 &hi, const SegInfo &g)
+{
+    ulonglong2 q;
+    q.x = pack21(q_down21(lo.x, g.rlo[0], g.h21[0]), q_down21(lo.y, g.rlo[1], g.h21[1]),
+                 q_down21(lo.z, g.rlo[2], g.h21[2]));
+    q.y = pack21(q_up21(hi.x, g.rlo[0], g.h21[0]), q_up21(hi.y, g.rlo[1], g.h21[1]),
+                 q_up21(hi.z, g.rlo[2], g.h21[2]));
+    return q;
+}
+
 // Rope of the subtree whose leaves end at `last` in tree [lo, hi]: the node
 // visited next in pre-order is the shallowest node starting at last + 1.  That
 // node is a right child, and a right child's Karras index is its first leaf,
@@ -438,7 +476,8 @@ template <bool WIDE, bool F32>
 __device__ __forceinline__ void fit_compute(const BuildArgs &a, int node, const int2 r, const int2 c, int rope,
                                             uint2 bl, uint2 br, const float4 &lo_a, const float4 &hi_a,
                                             const float4 &lo_b, const float4 &hi_b, uint2 *q_out, float4 *lo_out,
-                                            float4 *hi_out)
+                                            float4 *hi_out, const ulonglong2 &b21l, const ulonglong2 &b21r,
+                                            ulonglong2 *q21_out)
 {
     const unsigned qlo = qmin3(bl.x, br.x);
     const unsigned qhi = qmax3(bl.y, br.y);
@@ -451,6 +490,16 @@ __device__ __forceinline__ void fit_compute(const BuildArgs &a, int node, const 
     w.w = rope;
     __stcg(a.nodes + node, w);
     if (q_out) *q_out = make_uint2(qlo, qhi);
+    if (a.nodes21) {
+        // 21-bit bounds: per-field min / max of the children's (Sec. 2.2 at a
+        // wider bit width), the bundle flag in bit 63
+        const unsigned long long lo21 = qmin21(b21l.x, b21r.x), hi21 = qmax21(b21l.y, b21r.y);
+        if (q21_out) *q21_out = make_ulonglong2(lo21, hi21);
+        const unsigned long long lw = lo21 | ((unsigned long long)bundle << 63);
+        __stcg(a.nodes21 + 2 * (size_t)node,
+               make_int4((int)(unsigned)lw, (int)(unsigned)(lw >> 32), (int)(unsigned)hi21, (int)(unsigned)(hi21 >> 32)));
+        __stcg(a.nodes21 + 2 * (size_t)node + 1, make_int4(w.z, w.w, 0, 0));
+    }
     if (F32) {
         // exact FP32 AABB: min / max of the children's boxes (Fig. 3a layout)
         const float4 lo = make_float4(fminf(lo_a.x, lo_b.x), fminf(lo_a.y, lo_b.y), fminf(lo_a.z, lo_b.z), 0.f);
@@ -481,9 +530,27 @@ __device__ __forceinline__ void leaf_box(const BuildArgs &a, int k, float4 &lo, 
     }
 }
 
+// 21-bit box of internal node k as written in global memory
+__device__ __forceinline__ ulonglong2 node21_box(const BuildArgs &a, int k)
+{
+    const int4 w = __ldcg(a.nodes21 + 2 * (size_t)k);
+    const unsigned long long lo = ((unsigned long long)(unsigned)w.y << 32) | (unsigned)w.x;
+    const unsigned long long hi = ((unsigned long long)(unsigned)w.w << 32) | (unsigned)w.z;
+    return make_ulonglong2(lo & QBVH_QMASK21, hi);
+}
+
+// 21-bit box of leaf k (recomputed from the leaf's FP32 box)
+template <bool F64>
+__device__ __forceinline__ ulonglong2 leaf21_box(const BuildArgs &a, int k, const SegInfo &g)
+{
+    float4 lo, hi;
+    leaf_box<F64>(a, k, lo, hi);
+    return quantize21(make_float3(lo.x, lo.y, lo.z), make_float3(hi.x, hi.y, hi.z), g);
+}
+
 // Climb from `node` while this thread is the second arrival (global part).
 template <bool WIDE, bool F32, bool F64>
-__device__ __forceinline__ void fit_climb(const BuildArgs &a, int node, int hi)
+__device__ __forceinline__ void fit_climb(const BuildArgs &a, int node, int hi, int sg)
 {
     // a radix tree over 62-bit keys (30-bit code + 32-bit position) is at most
     // 63 levels deep; a longer walk means a broken parent link
@@ -534,14 +601,23 @@ __device__ __forceinline__ void fit_climb(const BuildArgs &a, int node, int hi)
                 leaf_box<F64>(a, ~c.y, lo_b, hi_b);
             }
         }
-        fit_compute<WIDE, F32>(a, node, r, c, rope, bl, br, lo_a, hi_a, lo_b, hi_b, nullptr, nullptr, nullptr);
+        ulonglong2 b21l = make_ulonglong2(0ull, 0ull), b21r = b21l;
+        if (a.nodes21) {
+            const SegInfo &g = a.seg[sg];
+            b21l = c.x >= 0 ? node21_box(a, c.x) : leaf21_box<F64>(a, ~c.x, g);
+            b21r = c.y >= 0 ? node21_box(a, c.y) : leaf21_box<F64>(a, ~c.y, g);
+        }
+        fit_compute<WIDE, F32>(a, node, r, c, rope, bl, br, lo_a, hi_a, lo_b, hi_b, nullptr, nullptr, nullptr, b21l,
+                               b21r, nullptr);
         node = up;
     }
 }
 
-template <bool WIDE, bool F32, bool F64>
-__global__ void __launch_bounds__(kBlock, 5) fit_kernel(const BuildArgs a)
+template <bool WIDE, bool F32, bool F64, bool Q21>
+__global__ void __launch_bounds__(kBlock, Q21 ? 4 : 5) fit_kernel(const BuildArgs a)
 {
+    __shared__ ulonglong2 s_q21[Q21 ? kBlock : 1];  // 21-bit box of internal node b0 + t
+    __shared__ ulonglong2 s_lq21[Q21 ? kBlock : 1]; // 21-bit box of leaf b0 + t
     __shared__ int s_done[kBlock];                  // local internal node b0 + t settled
     __shared__ uint2 s_q[kBlock];                   // quantized box of internal node b0 + t
     __shared__ uint2 s_lq[kBlock];                  // quantized box of leaf b0 + t
@@ -557,13 +633,13 @@ __global__ void __launch_bounds__(kBlock, 5) fit_kernel(const BuildArgs a)
     s_done[t] = 0;
 
     // ---- leaf k and the words of internal node k --------------------------
-    int hi = 0, leaf_up = -1;
+    int hi = 0, leaf_up = -1, sg = 0;
     bool node_valid = false;
     int2 r = make_int2(0, -1), c = make_int2(0, 0);
     int up = -1, rope = QBVH_END;
     if (live) {
         const unsigned long long key = key_at<WIDE>(a.keys_sorted, k);
-        const int sg = seg_of_key<WIDE>(key, a.n_types);
+        sg = seg_of_key<WIDE>(key, a.n_types);
         const SegInfo g = a.seg[sg];
         hi = g.start + g.count - 1;
         int orig = __ldg(a.order + k);
@@ -598,6 +674,7 @@ __global__ void __launch_bounds__(kBlock, 5) fit_kernel(const BuildArgs a)
         q.y = pack3(q_up(bhi.x, g.rlo[0], g.h[0]), q_up(bhi.y, g.rlo[1], g.h[1]), q_up(bhi.z, g.rlo[2], g.h[2]));
         a.leaf_q[k] = q;
         s_lq[t] = q;
+        if (Q21) s_lq21[t] = quantize21(blo, bhi, g);
         if (F32) {
             s_leaf[t] = F64 ? make_float4(blo.x, blo.y, blo.z, 0.f) : leaf;
             if (F64) s_leafhi[t] = make_float4(bhi.x, bhi.y, bhi.z, 0.f);
@@ -635,8 +712,14 @@ __global__ void __launch_bounds__(kBlock, 5) fit_kernel(const BuildArgs a)
                     lo_b = c.y >= 0 ? s_lo[ib] : s_leaf[ib];
                     hi_b = c.y >= 0 ? s_hi[ib] : (F64 ? s_leafhi[ib] : s_leaf[ib]);
                 }
+                ulonglong2 b21l = make_ulonglong2(0ull, 0ull), b21r = b21l;
+                if (Q21) {
+                    b21l = c.x >= 0 ? s_q21[ia] : s_lq21[ia];
+                    b21r = c.y >= 0 ? s_q21[ib] : s_lq21[ib];
+                }
                 fit_compute<WIDE, F32>(a, k, r, c, rope, bl, br, lo_a, hi_a, lo_b, hi_b, &s_q[t],
-                                       F32 ? &s_lo[t] : nullptr, F32 ? &s_hi[t] : nullptr);
+                                       F32 ? &s_lo[t] : nullptr, F32 ? &s_hi[t] : nullptr, b21l, b21r,
+                                       Q21 ? &s_q21[t] : nullptr);
                 done_now = true;
                 pending = false;
             }
@@ -652,13 +735,13 @@ __global__ void __launch_bounds__(kBlock, 5) fit_kernel(const BuildArgs a)
     // decides, and a parent's range contains its child's)
     if (live && leaf_up >= 0 && leaf_up < a.n) {
         const int2 pr = a.range[leaf_up];
-        if (!(pr.x >= b0 && pr.y <= b1)) fit_climb<WIDE, F32, F64>(a, leaf_up, hi);
+        if (!(pr.x >= b0 && pr.y <= b1)) fit_climb<WIDE, F32, F64>(a, leaf_up, hi, sg);
     } else if (live && leaf_up >= a.n) {
         atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
     }
     if (local && up >= 0 && up < a.n) {
         const int2 pr = a.range[up];
-        if (!(pr.x >= b0 && pr.y <= b1)) fit_climb<WIDE, F32, F64>(a, up, hi);
+        if (!(pr.x >= b0 && pr.y <= b1)) fit_climb<WIDE, F32, F64>(a, up, hi, sg);
     } else if (local && up >= a.n) {
         atomicOr(&a.status->err, QBVH_DEVERR_INTERNAL);
     }
@@ -707,14 +790,17 @@ void launch_fit(const BuildArgs &a, cudaStream_t s)
     if (a.n == 0) return;
     const int g = blocks_for(a.n, kBlock);
     if (a.wide_keys) {
-        if (a.nodes32) fit_kernel<true, true, false><<<g, kBlock, 0, s>>>(a);
-        else fit_kernel<true, false, false><<<g, kBlock, 0, s>>>(a);
+        if (a.nodes32) fit_kernel<true, true, false, false><<<g, kBlock, 0, s>>>(a);
+        else if (a.nodes21) fit_kernel<true, false, false, true><<<g, kBlock, 0, s>>>(a);
+        else fit_kernel<true, false, false, false><<<g, kBlock, 0, s>>>(a);
     } else if (a.pos64) {
-        if (a.nodes32) fit_kernel<false, true, true><<<g, kBlock, 0, s>>>(a);
-        else fit_kernel<false, false, true><<<g, kBlock, 0, s>>>(a);
+        if (a.nodes32) fit_kernel<false, true, true, false><<<g, kBlock, 0, s>>>(a);
+        else if (a.nodes21) fit_kernel<false, false, true, true><<<g, kBlock, 0, s>>>(a);
+        else fit_kernel<false, false, true, false><<<g, kBlock, 0, s>>>(a);
     } else {
-        if (a.nodes32) fit_kernel<false, true, false><<<g, kBlock, 0, s>>>(a);
-        else fit_kernel<false, false, false><<<g, kBlock, 0, s>>>(a);
+        if (a.nodes32) fit_kernel<false, true, false, false><<<g, kBlock, 0, s>>>(a);
+        else if (a.nodes21) fit_kernel<false, false, false, true><<<g, kBlock, 0, s>>>(a);
+        else fit_kernel<false, false, false, false><<<g, kBlock, 0, s>>>(a);
     }
 }
 

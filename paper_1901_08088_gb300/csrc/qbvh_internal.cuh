@@ -15,6 +15,11 @@
 //   nodes32  2 x float4 per internal node, the uncompressed layout of Fig. 3a:
 //            {lo.x (sign bit = bundle), lo.y, lo.z, left or first leaf},
 //            {hi.x, hi.y, hi.z, rope}; written only when that format is chosen
+//   nodes21  2 x int4 per internal node, bounds quantized to 21 bits per axis
+//            against the tree's 2^21 - 1 bins: lo64 = qx << 42 | qy << 21 | qz
+//            (bit 63 = bundle), hi64 alike, as {lo64 low, lo64 high, hi64 low,
+//            hi64 high}, {left or first leaf, rope, 0, 0}; written only when
+//            that format is chosen
 //   leaves   float4 {x, y, z, original index | rope-is-internal<<31}
 // Node ids: k >= 0 internal node k, ~k (negative) leaf k, QBVH_END = INT32_MIN.
 #pragma once
@@ -33,6 +38,9 @@
 // quantization: 2^10 - 1 bins per axis, bounds on the 1024 bin edges 0..1023
 #define QBVH_QMAX 1023
 #define QBVH_QMASK 0x3FFFFFFFu
+// 21-bit node format: 2^21 - 1 bins per axis, three fields in 63 bits
+#define QBVH_QMAX21 2097151
+#define QBVH_QMASK21 0x7FFFFFFFFFFFFFFFull
 
 namespace qbvh {
 
@@ -200,6 +208,23 @@ __device__ __forceinline__ LJPairGeom lj_pair_geom(const float4 &pi, const float
     return g;
 }
 
+// Outward snapping onto the 2^21 bin edges of the 21-bit node format (lower
+// bound rounded down, upper bound up, IEEE directed rounding), shared by the
+// build and by candidate mode's 21-bit leaf boxes.
+__device__ __forceinline__ unsigned q_down21(float x, float r, float h)
+{
+    float v = floorf(__fdiv_rd(__fsub_rd(x, r), h));
+    v = fminf(fmaxf(v, 0.f), (float)QBVH_QMAX21);
+    return (unsigned)v;
+}
+
+__device__ __forceinline__ unsigned q_up21(float x, float r, float h)
+{
+    float v = ceilf(__fdiv_ru(__fsub_ru(x, r), h));
+    v = fminf(fmaxf(v, 0.f), (float)QBVH_QMAX21);
+    return (unsigned)v;
+}
+
 // Per-segment (tree) information, written by the build.
 struct SegInfo {
     int start;      // first sorted position
@@ -210,6 +235,7 @@ struct SegInfo {
     float rhi[3];   // root AABB upper corner
     float h[3];     // bin width per axis, rounded up, >= FLT_MIN
     float pad;
+    float h21[3];   // bin width of the 21-bit node format (2^21 - 1 bins), rounded up
 };
 
 // Per-system information.
@@ -260,6 +286,7 @@ struct BuildArgs {
     uint2 *leaf_q;
     int4 *nodes;
     float4 *nodes32;     // [2n] FP32 nodes or nullptr
+    int4 *nodes21;       // [2n] 21-bit nodes or nullptr
     float4 *leaves;
     DevStatus *status;
 };
@@ -291,6 +318,7 @@ int sort_wait_selftest(int spin_limit, unsigned *err_out, cudaStream_t s);
 struct QueryArgs {
     const int4 *nodes;
     const float4 *nodes32;  // FP32 node format (node_fmt == 1)
+    const int4 *nodes21;    // 21-bit node format (node_fmt == 2)
     int node_fmt;
     const float4 *leaves;
     const uint2 *leaf_q;   // quantized leaf boxes (candidate mode)

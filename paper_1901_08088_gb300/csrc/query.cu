@@ -104,6 +104,30 @@ __device__ __forceinline__ Node decode_f(const float4 a, const float4 b)
     return n;
 }
 
+// 21-bit node (2 x int4 read as 8 floats): bounds decoded outward like the
+// 10-bit ones, fields x << 42 | y << 21 | z of two 64-bit words.
+__device__ __forceinline__ float q21_at(unsigned long long w, int shift)
+{
+    return __uint_as_float(((unsigned)(w >> shift) & (unsigned)QBVH_QMAX21) | 0x4B000000u) - 8388608.f;
+}
+
+__device__ __forceinline__ Node decode_21(const float4 a, const float4 b, const Frame &f)
+{
+    const unsigned long long lo = ((unsigned long long)__float_as_uint(a.y) << 32) | __float_as_uint(a.x);
+    const unsigned long long hi = ((unsigned long long)__float_as_uint(a.w) << 32) | __float_as_uint(a.z);
+    Node n;
+    n.lx = __fmaf_rd(q21_at(lo, 42), f.hx, f.rx);
+    n.ly = __fmaf_rd(q21_at(lo, 21), f.hy, f.ry);
+    n.lz = __fmaf_rd(q21_at(lo, 0), f.hz, f.rz);
+    n.hx = __fmaf_ru(q21_at(hi, 42), f.hx, f.rx);
+    n.hy = __fmaf_ru(q21_at(hi, 21), f.hy, f.ry);
+    n.hz = __fmaf_ru(q21_at(hi, 0), f.hz, f.rz);
+    n.left = __float_as_int(b.x);
+    n.rope = __float_as_int(b.y);
+    n.bundle = (lo >> 63) != 0ull;
+    return n;
+}
+
 // Read-only loads of tree words (nodes, leaves).  QBVH_TREE_EVICT_LAST = 1
 // marks them evict-last in L2, so that the list writes streaming through L2
 // (about 1.4 GB of DRAM writes per launch at N = 2M, against a 96 MB tree)
@@ -170,8 +194,10 @@ __device__ __forceinline__ Raw load_raw(const QueryArgs &A, int id)
     Raw r;
     if (FMT == 0) {
         r.q = tree_ld(A.nodes + id);
-    } else {
+    } else if (FMT == 1) {
         node32_ld(A.nodes32 + 2 * (size_t)id, r.a, r.b);
+    } else {
+        node32_ld(reinterpret_cast<const float4 *>(A.nodes21) + 2 * (size_t)id, r.a, r.b);
     }
     return r;
 }
@@ -180,7 +206,8 @@ template <int FMT>
 __device__ __forceinline__ Node decode(const Raw &r, const Frame &f)
 {
     if (FMT == 0) return decode_q(r.q, f);
-    return decode_f(r.a, r.b);
+    if (FMT == 1) return decode_f(r.a, r.b);
+    return decode_21(r.a, r.b, f);
 }
 
 // Sphere (centre p, squared radius rs2) against a box: lower bound of the
@@ -381,32 +408,57 @@ __device__ __forceinline__ void exact_leaf(const QueryArgs &A, const Query &c, R
     if (exact_accept<SHIFT, F64, SELF>(A, c, j, q)) out.push(__float_as_int(q.w) & 0x7FFFFFFF);
 }
 
-// Alg. 1 without the exact filter: list j when the sphere overlaps its
-// quantized leaf box (false positives included).
-__device__ __forceinline__ void candidate_leaf(const Query &c, Row &out, int j, const float4 q, const uint2 lq,
-                                               const Frame &f, float rs2)
+// Alg. 1 without the exact filter: the sphere against leaf j's box at the
+// node format's precision (Sec. 2.2): the 10-bit quantized box (FMT 0), the
+// FP32 point itself (FMT 1) or the 21-bit quantized box (FMT 2, snapped and
+// decoded outward against the tree's 21-bit frame f).
+template <int FMT>
+__device__ __forceinline__ bool cand_overlap(const QueryArgs &A, const Query &c, int j, const float4 q,
+                                             const Frame &f, float rs2)
 {
-    if (j != c.self && overlap_q(c.px, c.py, c.pz, lq, f, rs2)) out.push(__float_as_int(q.w) & 0x7FFFFFFF);
+    if (FMT == 0) return overlap_q(c.px, c.py, c.pz, __ldg(A.leaf_q + j), f, rs2);
+    Node n;
+    if (FMT == 1) {
+        n.lx = n.hx = q.x;
+        n.ly = n.hy = q.y;
+        n.lz = n.hz = q.z;
+    } else {
+        n.lx = __fmaf_rd((float)q_down21(q.x, f.rx, f.hx), f.hx, f.rx);
+        n.ly = __fmaf_rd((float)q_down21(q.y, f.ry, f.hy), f.hy, f.ry);
+        n.lz = __fmaf_rd((float)q_down21(q.z, f.rz, f.hz), f.hz, f.rz);
+        n.hx = __fmaf_ru((float)q_up21(q.x, f.rx, f.hx), f.hx, f.rx);
+        n.hy = __fmaf_ru((float)q_up21(q.y, f.ry, f.hy), f.hy, f.ry);
+        n.hz = __fmaf_ru((float)q_up21(q.z, f.rz, f.hz), f.hz, f.rz);
+    }
+    return overlap(c.px, c.py, c.pz, n, rs2);
 }
 
-template <bool CAND, bool SHIFT = true, bool F64 = false, bool SELF = true>
+// List j when the sphere overlaps its leaf box (false positives included).
+template <int FMT>
+__device__ __forceinline__ void candidate_leaf(const QueryArgs &A, const Query &c, Row &out, int j, const float4 q,
+                                               const Frame &f, float rs2)
+{
+    if (j != c.self && cand_overlap<FMT>(A, c, j, q, f, rs2)) out.push(__float_as_int(q.w) & 0x7FFFFFFF);
+}
+
+template <bool CAND, bool SHIFT = true, bool F64 = false, bool SELF = true, int FMT = 0>
 __device__ __forceinline__ void test_leaf(const QueryArgs &A, const Query &c, Row &out, int j, const float4 q,
                                           const Frame &f, float rs2)
 {
     if (CAND)
-        candidate_leaf(c, out, j, q, __ldg(A.leaf_q + j), f, rs2);
+        candidate_leaf<FMT>(A, c, out, j, q, f, rs2);
     else
         exact_leaf<SHIFT, F64, SELF>(A, c, out, j, q);
 }
 
 // The same decisions as exact_leaf / candidate_leaf, returned instead of
 // appended (used when several lanes share one particle's row).
-template <bool CAND, bool SHIFT, bool F64 = false>
+template <bool CAND, bool SHIFT, bool F64 = false, int FMT = 0>
 __device__ __forceinline__ bool leaf_accepts(const QueryArgs &A, const Query &c, int j, const float4 q,
                                              const Frame &f, float rs2)
 {
     if (j == c.self) return false;
-    if (CAND) return overlap_q(c.px, c.py, c.pz, __ldg(A.leaf_q + j), f, rs2);
+    if (CAND) return cand_overlap<FMT>(A, c, j, q, f, rs2);
     return exact_accept<SHIFT, F64>(A, c, j, q);
 }
 
@@ -470,6 +522,19 @@ __device__ __forceinline__ int seg_of_sorted(const QueryArgs &a, int s)
     if (WIDE) return (int)(__ldg(reinterpret_cast<const unsigned long long *>(a.keys_sorted) + s) >> 30);
     if (a.n_types > 1) return (int)(__ldg(reinterpret_cast<const unsigned *>(a.keys_sorted) + s) >> 30);
     return 0;
+}
+
+// the frame of the 21-bit node format: same corner, 2^21 - 1 bins
+__device__ __forceinline__ Frame frame21_of(const SegInfo &g)
+{
+    Frame f;
+    f.rx = g.rlo[0];
+    f.ry = g.rlo[1];
+    f.rz = g.rlo[2];
+    f.hx = g.h21[0];
+    f.hy = g.h21[1];
+    f.hz = g.h21[2];
+    return f;
 }
 
 __device__ __forceinline__ Frame frame_of(const SegInfo &g)
@@ -543,7 +608,7 @@ __global__ void query_thread_kernel(const __grid_constant__ QueryArgs a)
             if (g.count == 0) continue;
             c.rl2 = a.rl2[ta * T + tb];
             const float rs2 = a.rs2[ta * T + tb];
-            const Frame f = frame_of(g);
+            const Frame f = FMT == 2 ? frame21_of(g) : frame_of(g);
             unsigned mask = image_mask(me.x, me.y, me.z, L, g, rs2);
             const int root = g.count >= 2 ? g.start : ~g.start;
             const int last = g.start + g.count - 1;
@@ -568,7 +633,8 @@ __global__ void query_thread_kernel(const __grid_constant__ QueryArgs a)
                                     l = nd.left - 1;
                                 }
                                 for (int j = nd.left; j <= l; ++j)
-                                    test_leaf<CAND>(a, c, out, j, tree_ld(a.leaves + j), f, rs2);
+                                    test_leaf<CAND, true, false, true, FMT>(a, c, out, j, tree_ld(a.leaves + j), f,
+                                                                           rs2);
                                 node = nd.rope;
                             } else {
                                 node = nd.left;
@@ -579,7 +645,7 @@ __global__ void query_thread_kernel(const __grid_constant__ QueryArgs a)
                     } else {
                         const int j = ~node;
                         const float4 q = tree_ld(a.leaves + j);
-                        test_leaf<CAND>(a, c, out, j, q, f, rs2);
+                        test_leaf<CAND, true, false, true, FMT>(a, c, out, j, q, f, rs2);
                         node = (j == last) ? QBVH_END : ((__float_as_int(q.w) < 0) ? j + 1 : ~(j + 1));
                     }
                 }
@@ -913,7 +979,7 @@ __device__ __forceinline__ void bundle_filtered(const QueryArgs &a, const Query 
 #define QBVH_LEAF_PAIRS 1
 #endif
 // Every lane tests every leaf j..l of a bundle (one particle per lane).
-template <bool CAND, bool SHIFT, bool F64, bool SELF>
+template <bool CAND, bool SHIFT, bool F64, bool SELF, int FMT>
 __device__ __forceinline__ void bundle_loop(const QueryArgs &a, const Query &c, Row &out, int j, int l,
                                             const Frame &f, float rs2, bool on)
 {
@@ -922,14 +988,14 @@ __device__ __forceinline__ void bundle_loop(const QueryArgs &a, const Query &c, 
         const float4 q0 = tree_ld(a.leaves + j);
         const float4 q1 = tree_ld(a.leaves + j + 1);
         if (on) {
-            test_leaf<CAND, SHIFT, F64, SELF>(a, c, out, j, q0, f, rs2);
-            test_leaf<CAND, SHIFT, F64, SELF>(a, c, out, j + 1, q1, f, rs2);
+            test_leaf<CAND, SHIFT, F64, SELF, FMT>(a, c, out, j, q0, f, rs2);
+            test_leaf<CAND, SHIFT, F64, SELF, FMT>(a, c, out, j + 1, q1, f, rs2);
         }
     }
 #endif
     for (; j <= l; ++j) {
         const float4 q = tree_ld(a.leaves + j);
-        if (on) test_leaf<CAND, SHIFT, F64, SELF>(a, c, out, j, q, f, rs2);
+        if (on) test_leaf<CAND, SHIFT, F64, SELF, FMT>(a, c, out, j, q, f, rs2);
     }
 }
 
@@ -994,8 +1060,8 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                         if (self_here) bundle_spread<SHIFT, F64, true>(a, c, out, j, l - j + 1, hm);
                         else bundle_spread<SHIFT, F64, false>(a, c, out, j, l - j + 1, hm);
                     } else if (W == 1) {
-                        if (self_here || CAND) bundle_loop<CAND, SHIFT, F64, true>(a, c, out, j, l, f, rs2, on);
-                        else bundle_loop<CAND, SHIFT, F64, false>(a, c, out, j, l, f, rs2, on);
+                        if (self_here || CAND) bundle_loop<CAND, SHIFT, F64, true, FMT>(a, c, out, j, l, f, rs2, on);
+                        else bundle_loop<CAND, SHIFT, F64, false, FMT>(a, c, out, j, l, f, rs2, on);
                     } else {
                         // the W lanes of a particle take every W-th leaf
                         for (; j <= l; j += W) {
@@ -1004,7 +1070,7 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                             int id = 0;
                             if (jj <= l) {
                                 const float4 q = tree_ld(a.leaves + jj);
-                                acc = on && leaf_accepts<CAND, SHIFT, F64>(a, c, jj, q, f, rs2);
+                                acc = on && leaf_accepts<CAND, SHIFT, F64, FMT>(a, c, jj, q, f, rs2);
                                 id = __float_as_int(q.w) & 0x7FFFFFFF;
                             }
                             push_shared(out, acc, id, same);
@@ -1021,9 +1087,9 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
             const int j = ~node;
             const float4 q = tree_ld(a.leaves + j);
             if (W == 1) {
-                if (on) test_leaf<CAND, SHIFT, F64>(a, c, out, j, q, f, rs2);
+                if (on) test_leaf<CAND, SHIFT, F64, true, FMT>(a, c, out, j, q, f, rs2);
             } else {
-                const bool acc = wsub == 0 && on && leaf_accepts<CAND, SHIFT, F64>(a, c, j, q, f, rs2);
+                const bool acc = wsub == 0 && on && leaf_accepts<CAND, SHIFT, F64, FMT>(a, c, j, q, f, rs2);
                 push_shared(out, acc, __float_as_int(q.w) & 0x7FFFFFFF, same);
             }
             node = (j == last) ? QBVH_END : ((__float_as_int(q.w) < 0) ? j + 1 : ~(j + 1));
@@ -1127,7 +1193,7 @@ __device__ __forceinline__ void sparse_walks(const QueryArgs &a)
                 if (g.count == 0) continue;
                 c.rl2 = a.rl2[ta * T + tb];
                 const float rs2 = a.rs2[ta * T + tb];
-                const Frame f = frame_of(g);
+                const Frame f = FMT == 2 ? frame21_of(g) : frame_of(g);
                 const int root = g.count >= 2 ? g.start : ~g.start;
                 const int last = g.start + g.count - 1;
                 unsigned mask = image_mask(me.x, me.y, me.z, L, g, rs2);
@@ -1241,7 +1307,7 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
             }
             const float rs2 = a.rs2[ta * T + tb];
             const float rs = a.rs[ta * T + tb];
-            const Frame f = frame_of(g);
+            const Frame f = FMT == 2 ? frame21_of(g) : frame_of(g);
             const int root = g.count >= 2 ? g.start : ~g.start;
             const int last = g.start + g.count - 1;
             if (PHASE == 0) {
@@ -1372,12 +1438,14 @@ void launch_query(const QueryArgs &a, cudaStream_t s)
     if (a.n == 0) return;
     if (a.f64) {
         if (a.node_fmt == 0) launch_f64<0>(a, s);
-        else launch_f64<1>(a, s);
+        else if (a.node_fmt == 1) launch_f64<1>(a, s);
+        else launch_f64<2>(a, s);
         return;
     }
     if (a.traversal == 0) {
         if (a.node_fmt == 0) launch_thread<0>(a, s);
-        else launch_thread<1>(a, s);
+        else if (a.node_fmt == 1) launch_thread<1>(a, s);
+        else launch_thread<2>(a, s);
         return;
     }
     const int W = 32 / a.warp_particles;
@@ -1390,7 +1458,7 @@ void launch_query(const QueryArgs &a, cudaStream_t s)
         case 16: launch_warp<0, 16>(a, s); break;
         default: launch_warp<0, 32>(a, s); break;
         }
-    } else {
+    } else if (a.node_fmt == 1) {
         switch (W) {
         case 1: launch_warp<1, 1>(a, s); break;
         case 2: launch_warp<1, 2>(a, s); break;
@@ -1398,6 +1466,15 @@ void launch_query(const QueryArgs &a, cudaStream_t s)
         case 8: launch_warp<1, 8>(a, s); break;
         case 16: launch_warp<1, 16>(a, s); break;
         default: launch_warp<1, 32>(a, s); break;
+        }
+    } else {
+        switch (W) {
+        case 1: launch_warp<2, 1>(a, s); break;
+        case 2: launch_warp<2, 2>(a, s); break;
+        case 4: launch_warp<2, 4>(a, s); break;
+        case 8: launch_warp<2, 8>(a, s); break;
+        case 16: launch_warp<2, 16>(a, s); break;
+        default: launch_warp<2, 32>(a, s); break;
         }
     }
 }

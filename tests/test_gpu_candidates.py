@@ -1,8 +1,9 @@
 """Alg. 1 as written (no exact leaf test, Sec. 2.3): the GPU's candidate rows
 against the oracle's candidate lists (oracle/cand_ref.c), as multisets (an
-index once per periodic image that lists it), at the 10-bit quantized node
-format, where the walk reaches exactly the leaves whose quantized box the
-padded sphere overlaps.  Also the false positives per particle on the
+index once per periodic image that lists it).  Each node format tests the
+leaves at its own precision (10-bit box, FP32 point, 21-bit box; Sec. 2.2),
+and its internal boxes contain its leaf boxes, so the walk reaches exactly the
+leaves the oracle lists at that precision.  Also the false positives per particle on the
 paper's LJ state points (Sec. 4.1: N = 128,000, r_c = 3.0, rho 0.2 and 0.8;
 the paper reports about 1.5 and 3.8 per particle, ~5%), printed."""
 import numpy as np
@@ -24,13 +25,17 @@ def _assert_same_multisets(rg, cg, rc, cc):
     assert bad.size == 0, bad[:10]
 
 
+LEAF_BITS = {0: 10, 1: 0, 2: 21}   # node format -> precision of its leaf boxes
+
+
+@pytest.mark.parametrize("node_format", [0, 1, 2])
 @pytest.mark.parametrize("traversal,wp", [(0, 32), (1, 32), (1, 8), (1, 1)])
-@pytest.mark.parametrize("bundle", [1, 16, 32])
-def test_candidates_equal_oracle_config1(traversal, wp, bundle):
+@pytest.mark.parametrize("bundle", [1, 16, 32, 64])
+def test_candidates_equal_oracle_config1(traversal, wp, bundle, node_format):
     s = workloads.workload("lj_n4096_rho0.6", seed=0)
     rg, cg, nl, _ = gpu_list(s, candidates=1, cap=512, traversal=traversal, warp_particles=wp, bundle=bundle,
-                             node_format=0)
-    rc, cc = oracle.candidates(s.pos, s.L, s.r_list, cap=512)
+                             node_format=node_format)
+    rc, cc = oracle.candidates(s.pos, s.L, s.r_list, cap=512, leaf_bits=LEAF_BITS[node_format])
     _assert_same_multisets(rg, cg, rc, cc)
     nl.close()
 
@@ -44,10 +49,11 @@ def test_candidates_equal_oracle_three_types_per_pair_radii():
     types = rng.integers(0, 3, n).astype(np.int32)
     rl = np.array([[2.0, 2.5, 3.0], [2.5, 1.5, 0.0], [3.0, 0.0, 4.0]], np.float32)
     s = workloads.System(pos=pos, types=types, L=L, n_types=3, r_list=rl, r_cut=rl.copy())
-    rg, cg, nl, _ = gpu_list(s, candidates=1, cap=1024, node_format=0)
-    rc, cc = oracle.candidates(s.pos, s.L, s.r_list, s.types, s.n_types, cap=1024)
-    _assert_same_multisets(rg, cg, rc, cc)
-    nl.close()
+    for fmt in (0, 1, 2):
+        rg, cg, nl, _ = gpu_list(s, candidates=1, cap=1024, node_format=fmt)
+        rc, cc = oracle.candidates(s.pos, s.L, s.r_list, s.types, s.n_types, cap=1024, leaf_bits=LEAF_BITS[fmt])
+        _assert_same_multisets(rg, cg, rc, cc)
+        nl.close()
 
 
 def test_candidates_equal_oracle_two_type_lj():
@@ -59,19 +65,22 @@ def test_candidates_equal_oracle_two_type_lj():
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("node_format", [0, 2, 1])
 @pytest.mark.parametrize("rho", [0.2, 0.8])
-def test_false_positives_per_particle(rho):
+def test_false_positives_per_particle(rho, node_format):
     s = workloads.jittered_lattice(128_000, rho, 0.3, seed=1, r_cut=3.0, skin=0.0)
-    rg, cg, nl, _ = gpu_list(s, candidates=1, cap=512, node_format=0, bundle=32, block=256)
-    rc, cc = oracle.candidates(s.pos, s.L, s.r_list, cap=512)
+    rg, cg, nl, _ = gpu_list(s, candidates=1, cap=512, node_format=node_format, bundle=32, block=256)
+    bits = LEAF_BITS[node_format]
+    rc, cc = oracle.candidates(s.pos, s.L, s.r_list, cap=512, leaf_bits=bits)
     _assert_same_multisets(rg, cg, rc, cc)
     ro, co = oracle_list(s, cap=512)
     sets_o = oracle.rows_as_sets(ro, co)
     for i in range(0, s.n, 257):
         assert sets_o[i] <= set(rg[i, : cg[i]].tolist())
     fp = (cg.astype(np.int64) - co).mean()
-    print(f"rho {rho}: {co.mean():.2f} true neighbours, {fp:.2f} false positives per particle "
-          f"({100 * fp / co.mean():.1f}%), 10-bit quantized leaves")
+    kind = {10: "10-bit quantized", 21: "21-bit quantized", 0: "FP32"}[bits]
+    print(f"rho {rho}: {co.mean():.2f} true neighbours, {fp:.4f} false positives per particle "
+          f"({100 * fp / co.mean():.3f}%), {kind} leaves")
     assert (cg >= co).all()
-    assert 0.0 < fp / co.mean() < 0.25
+    assert fp / co.mean() < (0.25 if bits == 10 else 0.002)
     nl.close()

@@ -19,7 +19,7 @@ def cfg1():
     return workloads.workload("lj_n4096_rho0.6", seed=0)
 
 
-@pytest.mark.parametrize("node_format", [0, 1])
+@pytest.mark.parametrize("node_format", [0, 1, 2])
 @pytest.mark.parametrize("traversal,wp", [(0, 32), (1, 32), (1, 16), (1, 8), (1, 4), (1, 2), (1, 1)])
 @pytest.mark.parametrize("bundle,block", [(1, 128), (4, 128), (8, 64), (2, 256), (16, 128), (32, 32)])
 def test_config1_exact_list_equals_bruteforce(cfg1, bundle, block, traversal, node_format, wp):
@@ -31,7 +31,7 @@ def test_config1_exact_list_equals_bruteforce(cfg1, bundle, block, traversal, no
     nl.close()
 
 
-@pytest.mark.parametrize("node_format", [0, 1])
+@pytest.mark.parametrize("node_format", [0, 1, 2])
 @pytest.mark.parametrize("n", [4096, 12345, 33, 65, 1000])
 @pytest.mark.parametrize("bundle", [33, 48, 64])
 def test_bundles_wider_than_a_warp(bundle, n, node_format):
@@ -71,7 +71,8 @@ def _uniform(n, L, r, seed, n_types=1):
 
 
 @pytest.mark.parametrize("traversal,node_format,wp", [(0, 0, 32), (1, 0, 32), (1, 1, 32), (1, 0, 16), (1, 1, 8),
-                                                     (1, 1, 4), (1, 0, 2), (1, 1, 1)])
+                                                     (1, 1, 4), (1, 0, 2), (1, 1, 1), (1, 2, 32), (0, 2, 32),
+                                                     (1, 2, 4)])
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 31, 33, 255, 4095, 4097, 12345])
 def test_ragged_sizes(n, traversal, node_format, wp):
     L = max(8.0, (n / 0.5) ** (1 / 3))

@@ -39,7 +39,9 @@ def fluid_2m():
     dict(bundle=16, block=128, node_format=0, traversal=0, warp_particles=32),   # Alg. 1 one thread per particle
     dict(bundle=16, block=128, node_format=1, traversal=1, warp_particles=16),   # two lanes per particle
     dict(bundle=64, block=256, node_format=0, traversal=1, warp_particles=32),   # 64-leaf bundles
-], ids=["bench_fp32_nodes", "quantized_nodes", "thread_per_particle", "two_lanes_per_particle", "bundles_64"])
+    dict(bundle=64, block=256, node_format=2, traversal=1, warp_particles=32),   # 21-bit nodes
+], ids=["bench_fp32_nodes", "quantized_nodes", "thread_per_particle", "two_lanes_per_particle", "bundles_64",
+        "nodes_21bit"])
 def test_all_2m_rows_equal_cell_list(fluid_2m, opts):
     import torch
 
