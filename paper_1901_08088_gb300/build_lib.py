@@ -21,7 +21,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libqbvh.so")
 HEADERS = [os.path.join(CSRC, "qbvh_internal.cuh"), os.path.join(ROOT, "include", "qbvh.h")]
-SOURCES = ["api.cu", "build.cu", "sort.cu", "query.cu", "lj.cu", "noalloc.cu", "grid.cu"]
+SOURCES = ["api.cu", "build.cu", "sort.cu", "query.cu", "lj.cu", "noalloc.cu", "grid.cu", "small_build.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fsigned-char",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -21,6 +21,11 @@ namespace qbvh {
 int lj_particles_per_block();
 }
 
+// 1: one system of at most 3072 particles is built by one block (small_build.cu)
+#ifndef QBVH_SMALL_BUILD
+#define QBVH_SMALL_BUILD 1
+#endif
+
 namespace {
 
 // Named host ranges around each stage for timeline tools (NVTX; header-only,
@@ -322,16 +327,24 @@ int build_impl(qbvh_ctx *h, const void *pos_dev, int n, int n_sys, const int *of
     a.sort_passes = passes;
     h->built_fmt = h->node_fmt;
 
-    launch_build_prepare(a, s);
-    launch_morton(a, s);
-    launch_seg_scan(a, s);
-    h->sorted = radix_sort_pairs(h->wide, h->keys[0].p, h->keys[1].p, reinterpret_cast<int *>(h->vals[0].p),
-                                 reinterpret_cast<int *>(h->vals[1].p), n, bits, h->sort_scratch.p,
-                                 &a.status->err, s, /*prepared=*/true);
-    a.keys_sorted = h->keys[h->sorted].p;
-    a.order = reinterpret_cast<const int *>(h->vals[h->sorted].p);
-    launch_karras(a, s);
-    launch_fit(a, s);
+    if (QBVH_SMALL_BUILD && small_build_fits(a)) {
+        // one small system (small_build_fits): the whole build in one block
+        h->sorted = 0;
+        a.keys_sorted = h->keys[0].p;
+        a.order = reinterpret_cast<const int *>(h->vals[0].p);
+        launch_small_build(a, s);
+    } else {
+        launch_build_prepare(a, s);
+        launch_morton(a, s);
+        launch_seg_scan(a, s);
+        h->sorted = radix_sort_pairs(h->wide, h->keys[0].p, h->keys[1].p, reinterpret_cast<int *>(h->vals[0].p),
+                                     reinterpret_cast<int *>(h->vals[1].p), n, bits, h->sort_scratch.p,
+                                     &a.status->err, s, /*prepared=*/true);
+        a.keys_sorted = h->keys[h->sorted].p;
+        a.order = reinterpret_cast<const int *>(h->vals[h->sorted].p);
+        launch_karras(a, s);
+        launch_fit(a, s);
+    }
     rc = cuda_status();
     if (rc) return rc;
     h->built = true;

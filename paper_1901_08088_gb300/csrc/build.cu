@@ -30,25 +30,6 @@ constexpr int kBlock = 256;
 constexpr int kLocalSegs = 64;
 constexpr int kMortonItems = 8;   // particles per thread of the Morton pass
 
-__device__ __forceinline__ unsigned spread10(unsigned v)
-{
-    // place bit k of a 10-bit value at bit 3k
-    v &= 0x3FFu;
-    v = (v | (v << 16)) & 0x030000FFu;
-    v = (v | (v << 8)) & 0x0300F00Fu;
-    v = (v | (v << 4)) & 0x030C30C3u;
-    v = (v | (v << 2)) & 0x09249249u;
-    return v;
-}
-
-__device__ __forceinline__ unsigned bin_of(float x, float scale)
-{
-    int b = (int)__fmul_rn(x, scale);   // truncation == floor for x >= 0
-    b = b < 0 ? 0 : b;
-    b = b > QBVH_QMAX - 1 ? QBVH_QMAX - 1 : b;
-    return (unsigned)b;
-}
-
 __device__ __forceinline__ int sys_of(const int *off, int n_sys, int i)
 {
     // largest k with off[k] <= i
@@ -368,38 +349,6 @@ __global__ void __launch_bounds__(kBlock) karras_kernel(const BuildArgs a)
     if (i == lo) a.par_int[i] = -1;   // node lo of a tree is its root
 }
 
-__device__ __forceinline__ unsigned pack3(unsigned x, unsigned y, unsigned z)
-{
-    return (x << 20) | (y << 10) | z;
-}
-
-__device__ __forceinline__ unsigned qmin3(unsigned a, unsigned b)
-{
-    return pack3(min((a >> 20) & 1023u, (b >> 20) & 1023u), min((a >> 10) & 1023u, (b >> 10) & 1023u),
-                 min(a & 1023u, b & 1023u));
-}
-
-__device__ __forceinline__ unsigned qmax3(unsigned a, unsigned b)
-{
-    return pack3(max((a >> 20) & 1023u, (b >> 20) & 1023u), max((a >> 10) & 1023u, (b >> 10) & 1023u),
-                 max(a & 1023u, b & 1023u));
-}
-
-// Lower bound snapped down / upper bound snapped up onto the bin edges.
-__device__ __forceinline__ unsigned q_down(float x, float r, float h)
-{
-    float v = floorf(__fdiv_rd(__fsub_rd(x, r), h));
-    v = fminf(fmaxf(v, 0.f), (float)QBVH_QMAX);
-    return (unsigned)v;
-}
-
-__device__ __forceinline__ unsigned q_up(float x, float r, float h)
-{
-    float v = ceilf(__fdiv_ru(__fsub_ru(x, r), h));
-    v = fminf(fmaxf(v, 0.f), (float)QBVH_QMAX);
-    return (unsigned)v;
-}
-
 // 21-bit fields, three per 64-bit word (x << 42 | y << 21 | z)
 __device__ __forceinline__ unsigned long long pack21(unsigned x, unsigned y, unsigned z)
 {
@@ -432,18 +381,6 @@ __device__ __forceinline__ ulonglong2 quantize21(const float3 &lo, const float3 
     q.y = pack21(q_up21(hi.x, g.rlo[0], g.h21[0]), q_up21(hi.y, g.rlo[1], g.h21[1]),
                  q_up21(hi.z, g.rlo[2], g.h21[2]));
     return q;
-}
-
-// Rope of the subtree whose leaves end at `last` in tree [lo, hi]: the node
-// visited next in pre-order is the shallowest node starting at last + 1.  That
-// node is a right child, and a right child's Karras index is its first leaf,
-// so it is internal node last+1 if that node starts at last+1, else leaf last+1.
-__device__ __forceinline__ int rope_after(const int2 *range, int last, int hi)
-{
-    const int k = last + 1;
-    if (k > hi) return QBVH_END;
-    if (k <= hi - 1 && range[k].x == k) return k;
-    return ~k;
 }
 
 __device__ __forceinline__ float clear_sign(float x) { return __int_as_float(__float_as_int(x) & 0x7FFFFFFF); }

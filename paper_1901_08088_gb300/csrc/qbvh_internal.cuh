@@ -225,6 +225,70 @@ __device__ __forceinline__ unsigned q_up21(float x, float r, float h)
     return (unsigned)v;
 }
 
+// ---- build helpers shared by the multi-kernel and the one-block builds ----
+__device__ __forceinline__ unsigned spread10(unsigned v)
+{
+    // place bit k of a 10-bit value at bit 3k
+    v &= 0x3FFu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__device__ __forceinline__ unsigned bin_of(float x, float scale)
+{
+    int b = (int)__fmul_rn(x, scale);   // truncation == floor for x >= 0
+    b = b < 0 ? 0 : b;
+    b = b > QBVH_QMAX - 1 ? QBVH_QMAX - 1 : b;
+    return (unsigned)b;
+}
+
+__device__ __forceinline__ unsigned pack3(unsigned x, unsigned y, unsigned z)
+{
+    return (x << 20) | (y << 10) | z;
+}
+
+__device__ __forceinline__ unsigned qmin3(unsigned a, unsigned b)
+{
+    return pack3(min((a >> 20) & 1023u, (b >> 20) & 1023u), min((a >> 10) & 1023u, (b >> 10) & 1023u),
+                 min(a & 1023u, b & 1023u));
+}
+
+__device__ __forceinline__ unsigned qmax3(unsigned a, unsigned b)
+{
+    return pack3(max((a >> 20) & 1023u, (b >> 20) & 1023u), max((a >> 10) & 1023u, (b >> 10) & 1023u),
+                 max(a & 1023u, b & 1023u));
+}
+
+// Lower bound snapped down / upper bound snapped up onto the bin edges.
+__device__ __forceinline__ unsigned q_down(float x, float r, float h)
+{
+    float v = floorf(__fdiv_rd(__fsub_rd(x, r), h));
+    v = fminf(fmaxf(v, 0.f), (float)QBVH_QMAX);
+    return (unsigned)v;
+}
+
+__device__ __forceinline__ unsigned q_up(float x, float r, float h)
+{
+    float v = ceilf(__fdiv_ru(__fsub_ru(x, r), h));
+    v = fminf(fmaxf(v, 0.f), (float)QBVH_QMAX);
+    return (unsigned)v;
+}
+
+// Rope of the subtree whose leaves end at `last` in tree [lo, hi]: the node
+// visited next in pre-order is the shallowest node starting at last + 1.  That
+// node is a right child, and a right child's Karras index is its first leaf,
+// so it is internal node last+1 if that node starts at last+1, else leaf last+1.
+__device__ __forceinline__ int rope_after(const int2 *range, int last, int hi)
+{
+    const int k = last + 1;
+    if (k > hi) return QBVH_END;
+    if (k <= hi - 1 && range[k].x == k) return k;
+    return ~k;
+}
+
 // Per-segment (tree) information, written by the build.
 struct SegInfo {
     int start;      // first sorted position
@@ -296,6 +360,10 @@ void launch_morton(const BuildArgs &a, cudaStream_t s);
 void launch_seg_scan(const BuildArgs &a, cudaStream_t s);
 void launch_karras(const BuildArgs &a, cudaStream_t s);
 void launch_fit(const BuildArgs &a, cudaStream_t s);
+// one-block build of one small system (small_build.cu): whether it applies,
+// and the launch (writes sorted keys / order to keys_sorted / order)
+bool small_build_fits(const BuildArgs &a);
+void launch_small_build(const BuildArgs &a, cudaStream_t s);
 
 // ---- radix sort (sort.cu) ------------------------------------------------
 struct SortScratch {

@@ -289,3 +289,33 @@ def test_spinodal_like_1m():
     idx = np.sort(np.random.default_rng(1).choice(s.n, 8192, replace=False))
     assert_same_lists(rg, cg, ro, co, idx=idx)
     nl.close()
+
+
+@pytest.mark.parametrize("n_types", [1, 2, 4])
+@pytest.mark.parametrize("n,K", [(2, 1), (3, 16), (33, 4), (1000, 16), (3072, 64), (3073, 32), (4096, 32)])
+def test_small_system_tree_words_and_lists(n, K, n_types):
+    # one system of at most 3072 particles is built by a single block, larger
+    # ones by the multi-kernel build: the words of both must equal the
+    # oracle's step-by-step construction, per type tree
+    import torch
+
+    L = max(6.0, (n / 0.5) ** (1 / 3))
+    s = _uniform(n, L, 2.0, seed=7 * n + K, n_types=n_types)
+    for node_format in (0, 1):
+        rg, cg, nl, _ = gpu_list(s, bundle=K, node_format=node_format)
+        ro, co = oracle_list(s, method="brute")
+        assert_same_lists(rg, cg, ro, co)
+        t = {k: v.cpu() for k, v in nl.tree().items()}
+        o = oracle.lbvh_build(s.pos, s.types, [s.L] * n_types, bundle_k=K)
+        assert np.array_equal(t["order"].numpy(), o["order"])
+        assert np.array_equal(t["seg_start"].numpy(), o["seg_start"])
+        assert np.array_equal(t["leaves"].view(torch.int32).numpy(), o["leaves"].view(np.int32))
+        starts = o["seg_start"]
+        for tr in range(n_types):   # internal slots of every tree but its last leaf's
+            a, b = starts[tr], starts[tr + 1] - 1
+            if b > a:
+                assert np.array_equal(t["nodes"].numpy()[a:b], o["nodes"][a:b])
+        # frames of the non-empty trees (an empty tree's frame is never read)
+        full = np.diff(starts) > 0
+        assert np.array_equal(t["frames"].numpy()[full, :6].view(np.int32), o["frame"][full].view(np.int32))
+        nl.close()
