@@ -107,12 +107,12 @@ class ClockSampler:
 # options of each entry and the traversal sources whose SHA-256 prefix is given; any
 # other source or options report null.
 PROFILED_TRAFFIC = {
-    "source_sha256": "f2fae501d56e292f",
+    "source_sha256": "601be1c201b2f701",
     "entries": [
-        {"options": {"bundle_k": 16, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
-         "bytes": 485.67e6 + 1.36e9, "warp_inst": 1855300452},
-        {"options": {"bundle_k": 32, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
-         "bytes": 456.89e6 + 1.36e9, "warp_inst": 1797928799},
+        {"options": {"bundle_k": 64, "node_format": 0, "traversal": 1, "warp_particles": 32, "query_block": 256},
+         "bytes": 103.08e6 + 990.69e6, "warp_inst": 1711776670},
+        {"options": {"bundle_k": 64, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
+         "bytes": 102.99e6 + 992.95e6, "warp_inst": 1630920430},
     ],
 }
 # kernels of one timed step: build = prepare, Morton (+ sort histograms), segment
@@ -557,8 +557,8 @@ def run_grid_comparison(args, local):
             s = workloads.jittered_lattice(n, rho, jit, seed=0, r_cut=rc, skin=skin)
         pos4 = torch.from_numpy(workloads.pack_float4(s.pos, s.types)).cuda()
         res = {"workload": label, "n": n, "rho": rho, "r_list": float(s.r_list[0, 0])}
-        for method, space in ((0, {_lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8, 4, 1], _lib.QBVH_OPT_BUNDLE: [8, 16],
-                                    _lib.QBVH_OPT_NODE_FORMAT: [1, 0]}),
+        for method, space in ((0, {_lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8, 4, 1],
+                                    _lib.QBVH_OPT_BUNDLE: [8, 16, 32, 64], _lib.QBVH_OPT_NODE_FORMAT: [0, 1]}),
                               (1, {_lib.QBVH_OPT_GRID_LANES: [2, 4, 8, 16]})):
             nl = NeighborList(local)
             nl.set_option(_lib.QBVH_OPT_METHOD, method)
