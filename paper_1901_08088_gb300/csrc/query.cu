@@ -272,14 +272,21 @@ __device__ __forceinline__ void row_store(int *p, int v)
 // one 16-byte store was measured slower: the extra selects and registers cost
 // more than the narrower stores.)
 // Row staging (QBVH_ROW_STAGING = 1): a lane's entries first go to its
-// slot of a per-warp ring in shared memory, one 32-byte sector (8 entries)
-// per lane, slot k of lane l at ring[32 k + l] (conflict-free).  When the
-// count reaches a multiple of 8 the lane writes the completed sector with two
-// 16-byte stores; the partial last sector is written at the end of the
-// particle's walks.  Rows start on 32-byte boundaries (the row capacity is a
-// multiple of 8), so every sector write fills one whole DRAM sector, and the
-// L2 sees one write per 8 entries instead of one per entry.  Measured at
-// N = 2M before staging: the 4-byte row stores took 0.62 of 1.91 ms.
+// slots of a per-warp ring in shared memory, 16 entries (two 32-byte
+// sectors) per lane, slot k of lane l at ring[32 k + l] (conflict-free).
+// Rows start on 32-byte boundaries (the row capacity is a multiple of 8), so
+// a completed sector of 8 entries leaves with two 16-byte stores that fill
+// one whole DRAM sector, and the L2 sees one write per 8 entries instead of
+// one per entry.  The survivor loop (below) stages every tested survivor
+// without a branch (the slot after the last entry is free, and the count
+// only advances on acceptance) and checks for completed sectors once per 8
+// survivors and at the end of each chunk, so the lanes that completed one
+// write it together; with one ring sector of slack, at most one sector is
+// complete at a check.  Other pushes write a completed sector at once.  The
+// partial last sector is written at the end of the particle's walks.
+// Measured at N = 2M: the 4-byte row stores took 0.62 of 1.91 ms before
+// staging; a flush on every sector completion issued the sector write for
+// one or two lanes at a time, on most survivors.
 #ifndef QBVH_ROW_STAGING
 #define QBVH_ROW_STAGING 1
 #endif
@@ -296,25 +303,49 @@ struct Row {
     int cap;
     int count;
     int *ring;   // this lane's slot 0 in the warp's staging ring, or nullptr
+    int base;    // staging: entries [0, base) have left the ring (a multiple of 8)
 
+    // the completed sector [base, base + 8) (staging only)
+    __device__ __forceinline__ void flush()
+    {
+        if (base + 8 <= cap) store_sector(row + base, ring + 32 * (base & 15));
+        base += 8;
+    }
+
+    // a completed sector, if any (staging only; at most one between checks)
+    __device__ __forceinline__ void check()
+    {
+        if (count - base >= 8) flush();
+    }
+
+    // entry j, tested by the caller
     __device__ __forceinline__ void push(int j)
     {
         if (ring) {
-            if (count < cap) ring[32 * (count & 7)] = j;
+            ring[32 * (count & 15)] = j;
             ++count;
-            if ((count & 7) == 0 && count <= cap) store_sector(row + count - 8, ring);
+            check();
             return;
         }
         if (count < cap) row_store(row + count, j);
         ++count;
     }
 
+    // entry j if acc, without a branch (staging only; the caller checks
+    // within every 8 staged candidates)
+    __device__ __forceinline__ void stage(int j, bool acc)
+    {
+        ring[32 * (count & 15)] = j;
+        count += acc ? 1 : 0;
+    }
+
     // the entries of the last, partial sector (staging only)
     __device__ __forceinline__ void drain()
     {
         if (!ring) return;
+        check();
         const int end = min(count, cap);
-        for (int k = end & ~7; k < end; ++k) row_store(row + k, ring[32 * (k & 7)]);
+        for (int k = base; k < end; ++k) row_store(row + k, ring[32 * (k & 15)]);
     }
 };
 
@@ -600,6 +631,7 @@ __global__ void query_thread_kernel(const __grid_constant__ QueryArgs a)
         out.cap = a.cap;
         out.count = 0;
         out.ring = nullptr;
+        out.base = 0;
 
         for (int tb = 0; tb < T; ++tb) {
             const float rl = a.r_list[ta * T + tb];
@@ -812,12 +844,20 @@ __device__ __forceinline__ bool cube_overlap(unsigned nlo, unsigned nhi, const L
 #ifndef QBVH_LOOP_COST
 #define QBVH_LOOP_COST 14
 #endif
+// the walks that filter bundles (one particle per lane, exact lists of FP32 data)
+__host__ __device__ constexpr bool stage_on(int W, bool CAND, bool F64)
+{
+    return QBVH_PREFILTER && W == 1 && !CAND && !F64;
+}
+
 struct BundleStage {
     float4 blo, bhi;      // the warp's box of image centres (x, y, z)
     float x[32], y[32], z[32];
     int id[32];           // original indices of the survivors
-    int owner[32];        // overlapping lanes, in lane order (spread)
-    int ring[8 * 32];     // row staging: slot k of lane l at ring[32 k + l]
+    union {
+        int owner[32];    // overlapping lanes, in lane order (spread, without staging)
+        int ring[16 * 32];   // row staging: slot k of lane l at ring[32 k + l]
+    };
 };
 
 // Box of the image centres fl(x_i + n L) of the lanes that walk this image.
@@ -841,42 +881,69 @@ __device__ __forceinline__ void packet_box(const Query &c, bool on, BundleStage 
     __syncwarp();
 }
 
+template <bool SHIFT, bool SELF>
+__device__ __forceinline__ void survivor_pair(const Query &c, Row &out, int t, bool on, const BundleStage *st,
+                                              bool staged)
+{
+    const f32x2 X = *reinterpret_cast<const f32x2 *>(st->x + t);
+    const f32x2 Y = *reinterpret_cast<const f32x2 *>(st->y + t);
+    const f32x2 Z = *reinterpret_cast<const f32x2 *>(st->z + t);
+    const int2 id = *reinterpret_cast<const int2 *>(st->id + t);
+    f32x2 dx = f2_sub(X, f2_pack(c.xi, c.xi)), dy = f2_sub(Y, f2_pack(c.yi, c.yi)),
+          dz = f2_sub(Z, f2_pack(c.zi, c.zi));
+    if (SHIFT) {
+        dx = f2_sub(dx, f2_pack(c.nLx, c.nLx));
+        dy = f2_sub(dy, f2_pack(c.nLy, c.nLy));
+        dz = f2_sub(dz, f2_pack(c.nLz, c.nLz));
+    }
+    float sx0, sx1, sy0, sy1, sz0, sz1;
+    f2_unpack(f2_mul(dx, dx), sx0, sx1);
+    f2_unpack(f2_mul(dy, dy), sy0, sy1);
+    f2_unpack(f2_mul(dz, dz), sz0, sz1);
+    const float d0 = __fadd_rn(__fadd_rn(sx0, sy0), sz0);
+    const float d1 = __fadd_rn(__fadd_rn(sx1, sy1), sz1);
+    const bool a0 = on && d0 < c.rl2 && (!SELF || id.x != c.self_id);
+    const bool a1 = on && d1 < c.rl2 && (!SELF || id.y != c.self_id);
+    if (staged) {
+        out.stage(id.x, a0);
+        out.stage(id.y, a1);
+    } else {
+        if (a0) out.push(id.x);
+        if (a1) out.push(id.y);
+    }
+}
+
 // Every lane tests every survivor (one particle per lane), two per step: the
 // differences and squares as packed f32x2 pairs, the two sums as scalar adds
 // -- the same operations in the same order as exact_d2.  (ptxas contracts a
 // packed mul.rn.f32x2 feeding a packed add.rn.f32x2 into one fused
 // multiply-add, which changes the rounding of d2: measured on GB300, 8 rows
 // of the N = 2M list differed at d = r_list.  Scalar add.rn is not contracted.)
+// With row staging the accepted entries are staged without a branch and the
+// completed sectors written once per 8 survivors and at the end.
 template <bool SHIFT, bool SELF>
 __device__ __forceinline__ void survivors_loop(const Query &c, Row &out, int s, bool on, const BundleStage *st)
 {
-    const f32x2 xi2 = f2_pack(c.xi, c.xi), yi2 = f2_pack(c.yi, c.yi), zi2 = f2_pack(c.zi, c.zi);
+    const bool staged = out.ring != nullptr;
     int t = 0;
-    for (; t + 1 < s; t += 2) {
-        const f32x2 X = *reinterpret_cast<const f32x2 *>(st->x + t);
-        const f32x2 Y = *reinterpret_cast<const f32x2 *>(st->y + t);
-        const f32x2 Z = *reinterpret_cast<const f32x2 *>(st->z + t);
-        const int2 id = *reinterpret_cast<const int2 *>(st->id + t);
-        f32x2 dx = f2_sub(X, xi2), dy = f2_sub(Y, yi2), dz = f2_sub(Z, zi2);
-        if (SHIFT) {
-            dx = f2_sub(dx, f2_pack(c.nLx, c.nLx));
-            dy = f2_sub(dy, f2_pack(c.nLy, c.nLy));
-            dz = f2_sub(dz, f2_pack(c.nLz, c.nLz));
+    if (staged) {
+        for (; t + 8 <= s; t += 8) {
+            survivor_pair<SHIFT, SELF>(c, out, t, on, st, true);
+            survivor_pair<SHIFT, SELF>(c, out, t + 2, on, st, true);
+            survivor_pair<SHIFT, SELF>(c, out, t + 4, on, st, true);
+            survivor_pair<SHIFT, SELF>(c, out, t + 6, on, st, true);
+            out.check();
         }
-        float sx0, sx1, sy0, sy1, sz0, sz1;
-        f2_unpack(f2_mul(dx, dx), sx0, sx1);
-        f2_unpack(f2_mul(dy, dy), sy0, sy1);
-        f2_unpack(f2_mul(dz, dz), sz0, sz1);
-        const float d0 = __fadd_rn(__fadd_rn(sx0, sy0), sz0);
-        const float d1 = __fadd_rn(__fadd_rn(sx1, sy1), sz1);
-        if (on && d0 < c.rl2 && (!SELF || id.x != c.self_id)) out.push(id.x);
-        if (on && d1 < c.rl2 && (!SELF || id.y != c.self_id)) out.push(id.y);
     }
+    for (; t + 1 < s; t += 2) survivor_pair<SHIFT, SELF>(c, out, t, on, st, staged);
     if (t < s) {
         const float4 q = make_float4(st->x[t], st->y[t], st->z[t], 0.f);
         const int id = st->id[t];
-        if (on && exact_d2<SHIFT>(c, q) < c.rl2 && (!SELF || id != c.self_id)) out.push(id);
+        const bool acc = on && exact_d2<SHIFT>(c, q) < c.rl2 && (!SELF || id != c.self_id);
+        if (staged) out.stage(id, acc);
+        else if (acc) out.push(id);
     }
+    if (staged) out.check();
 }
 
 // Survivors spread over the warp when few lanes overlap the bundle: the s
@@ -1013,7 +1080,7 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                                           unsigned same, BundleStage *st = nullptr, float rs = 0.f)
 {
     // bundles filtered against the warp's box (one particle per lane, exact lists of FP32 data)
-    constexpr bool FILTER = QBVH_PREFILTER && W == 1 && !CAND && !F64;
+    constexpr bool FILTER = stage_on(W, CAND, F64);
     // 10-bit nodes tested in the integer domain on the same walks
     constexpr bool QCUBE = FILTER && FMT == 0 && QBVH_QCUBE;
     if (FILTER) packet_box(c, on, st);
@@ -1187,6 +1254,7 @@ __device__ __forceinline__ void sparse_walks(const QueryArgs &a)
             out.cap = a.cap;
             out.count = 0;
             out.ring = nullptr;
+            out.base = 0;
             for (int tb = 0; tb < T; ++tb) {
                 if (!(a.r_list[ta * T + tb] > 0.f)) continue;
                 const SegInfo g = a.seg[tb];
@@ -1271,12 +1339,14 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
     out.row = a.rows + (size_t)i_orig * a.cap;
     out.cap = a.cap;
     out.count = (PHASE == 1 && active) ? a.counts[i_orig] : 0;
-    constexpr bool STAGE = QBVH_PREFILTER && W == 1 && !CAND && !F64;
-    __shared__ BundleStage stage[STAGE ? 256 / 32 : 1];
+    constexpr bool STAGE = stage_on(W, CAND, F64);
+    // one BundleStage per warp, in dynamic shared memory sized to the block
+    extern __shared__ BundleStage stage[];
     BundleStage *st = STAGE ? &stage[threadIdx.x >> 5] : nullptr;
     // row staging on the filtered walks (every push of those walks goes through it)
     constexpr bool RING = STAGE && QBVH_ROW_STAGING && PHASE == 2;
     out.ring = RING ? st->ring + lane : nullptr;
+    out.base = 0;
     bool walked = PHASE != 1;
     bool elsewhere = false;   // particle of a sparse tree: walked by the leading blocks
     const int T = ONE ? 1 : a.n_types;
@@ -1373,6 +1443,12 @@ static int sparse_blocks_for(const QueryArgs &a)
     return sm_count_current() * (256 / a.block);
 }
 
+// dynamic shared memory of a traversal block: one BundleStage per warp
+static size_t stage_bytes(int block, bool stage)
+{
+    return stage ? (size_t)(block / 32) * sizeof(BundleStage) : 0;
+}
+
 template <int FMT, int W, int PHASE>
 static void launch_warp_phase(QueryArgs a, cudaStream_t s, int grid)
 {
@@ -1382,15 +1458,16 @@ static void launch_warp_phase(QueryArgs a, cudaStream_t s, int grid)
         a.sparse_blocks = sparse_blocks_for(a);
         grid += a.sparse_blocks;
     }
+    const size_t sm = stage_bytes(b, stage_on(W, a.candidates != 0, false));
     if (a.wide_keys) {
-        if (a.candidates) query_warp_kernel<true, true, FMT, W, false, PHASE><<<grid, b, 0, s>>>(a);
-        else query_warp_kernel<true, false, FMT, W, false, PHASE><<<grid, b, 0, s>>>(a);
+        if (a.candidates) query_warp_kernel<true, true, FMT, W, false, PHASE><<<grid, b, sm, s>>>(a);
+        else query_warp_kernel<true, false, FMT, W, false, PHASE><<<grid, b, sm, s>>>(a);
     } else if (a.candidates) {
-        query_warp_kernel<false, true, FMT, W, false, PHASE><<<grid, b, 0, s>>>(a);
+        query_warp_kernel<false, true, FMT, W, false, PHASE><<<grid, b, sm, s>>>(a);
     } else if (a.n_types == 1) {
-        query_warp_kernel<false, false, FMT, W, true, PHASE><<<grid, b, 0, s>>>(a);
+        query_warp_kernel<false, false, FMT, W, true, PHASE><<<grid, b, sm, s>>>(a);
     } else {
-        query_warp_kernel<false, false, FMT, W, false, PHASE><<<grid, b, 0, s>>>(a);
+        query_warp_kernel<false, false, FMT, W, false, PHASE><<<grid, b, sm, s>>>(a);
     }
 }
 
@@ -1429,8 +1506,9 @@ static void launch_f64(const QueryArgs &a, cudaStream_t s)
 {
     const int b = a.block;
     const int grid = (int)(((long long)((a.n + 31) / 32) * 32 + b - 1) / b);
-    if (a.n_types == 1) query_warp_kernel<false, false, FMT, 1, true, 2, true><<<grid, b, 0, s>>>(a);
-    else query_warp_kernel<false, false, FMT, 1, false, 2, true><<<grid, b, 0, s>>>(a);
+    const size_t sm = stage_bytes(b, stage_on(1, false, true));
+    if (a.n_types == 1) query_warp_kernel<false, false, FMT, 1, true, 2, true><<<grid, b, sm, s>>>(a);
+    else query_warp_kernel<false, false, FMT, 1, false, 2, true><<<grid, b, sm, s>>>(a);
 }
 
 void launch_query(const QueryArgs &a, cudaStream_t s)
