@@ -119,6 +119,8 @@ PROFILED_TRAFFIC = {
 # scan, 4 onesweep passes (30-bit keys, 8-bit digits), Karras, fit; query = 1
 # traversal launch (all periodic images); LJ = forward + fixed-order FP64 finalize
 KERNELS_PER_STEP = 9 + 1 + 2
+# with the LJ terms summed inside the traversal: build, traversal, finalize
+KERNELS_PER_STEP_FUSED = 9 + 1 + 1
 _TRAFFIC_SOURCES = ("paper_1901_08088_gb300/csrc/query.cu", "paper_1901_08088_gb300/csrc/qbvh_internal.cuh")
 
 
@@ -216,10 +218,12 @@ def run_ours(args):
     rc = np.full((1, 1), R_CUT, np.float32)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    # one step: build, then the traversal and the LJ energy/forces over its
+    # list through qbvh_query_lj_async (LJ terms inside the traversal when
+    # QBVH_OPT_FUSED_LJ = 1, else the traversal and the list pass back to back)
     def step(p4):
         nl.build(p4, s.L)
-        nl.query(s.r_list, cap=CAP)
-        check(qbvh_lj_forward(nl.h, p4, eps, sig, rc, None, U, F, None, None), "lj")
+        nl.query_lj_async(p4, s.r_list, CAP, eps, sig, rc, None, U, F, None, None)
 
     # options: explicit flags win; otherwise the autotuner picks them during
     # warm-up (the paper tunes launch parameters at run time, then freezes them)
@@ -238,13 +242,17 @@ def run_ours(args):
         explicit[_lib.QBVH_OPT_LJ_LANES] = args.lj_lanes
     if args.lj_zorder >= 0:
         explicit[_lib.QBVH_OPT_LJ_ZORDER] = args.lj_zorder
+    if args.fused_lj >= 0:
+        explicit[_lib.QBVH_OPT_FUSED_LJ] = args.fused_lj
     tuned, tune_evals = dict(explicit), 0
     if not args.no_autotune:
         def tune_step(opts):
             for k, v in opts.items():
                 nl.set_option(k, v)
             step(pos4)
-        space = {k: v for k, v in autotune.OPTION_SPACE.items() if k not in explicit}
+        full = dict(autotune.OPTION_SPACE)
+        full[_lib.QBVH_OPT_FUSED_LJ] = autotune.OPTIONAL_SPACE[_lib.QBVH_OPT_FUSED_LJ]
+        space = {k: v for k, v in full.items() if k not in explicit}
         tuned, _, log = autotune.tune(tune_step, space=space, start=explicit, reps=3, warmup=1, sweeps=2)
         tune_evals = len(log)
     for k, v in tuned.items():
@@ -253,11 +261,15 @@ def run_ours(args):
     for _ in range(args.warmup):
         step(pos4)
     torch.cuda.synchronize()
+    rc_q, _ = nl.query_status()
+    if rc_q != 0:
+        raise RuntimeError(f"query failed in warm-up: {_lib.QBVHError(rc_q)}")
+    fused = nl.get_option(_lib.QBVH_OPT_FUSED_LJ) == 1
     mean_nbrs = float(nl.neighbors()[1].double().mean().item())
     total_nbrs = int(nl.neighbors()[1].long().sum().item())
 
     stream = torch.cuda.current_stream()
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     sampler = ClockSampler(local)
     if world > 1:
         dist.barrier()
@@ -266,14 +278,12 @@ def run_ours(args):
     t0 = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(float(k))
-        e0, e1, e2, e3 = ev[k]
+        e0, e1, e2 = ev[k]
         e0.record(stream)
         nl.build(pos4, s.L)
         e1.record(stream)
-        nl.query_async(s.r_list, CAP)
+        nl.query_lj_async(pos4, s.r_list, CAP, eps, sig, rc, None, U, F, None, None)
         e2.record(stream)
-        check(qbvh_lj_forward(nl.h, pos4, eps, sig, rc, None, U, F, None, None), "lj")
-        e3.record(stream)
         # the query's status, once the step has run (outside the events): a
         # failed or overflowed query invalidates the step
         stream.synchronize()
@@ -284,10 +294,39 @@ def run_ours(args):
     wall = time.perf_counter() - t0
     clocks = sampler.stop()
     t_build = np.array([ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)])
-    t_query = np.array([ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)])
-    t_lj = np.array([ev[k][2].elapsed_time(ev[k][3]) for k in range(args.steps)])
-    t_step = t_build + t_query + t_lj
+    t_qlj = np.array([ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)])
+    t_step = t_build + t_qlj
     total_ms = max_over_ranks(float(t_step.sum()))
+
+    # the same options with the traversal and the list pass as two launches,
+    # each timed on its own: the list's build + query time (the metric's
+    # neighbor-list part) and the plain traversal's roofline
+    def split_times(reps):
+        nl.set_option(_lib.QBVH_OPT_FUSED_LJ, 0)
+        for _ in range(3):
+            step(pos4)
+        tb, tq, tl = [], [], []
+        for k in range(reps):
+            flush.fill_(float(k))
+            f = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            f[0].record(stream)
+            nl.build(pos4, s.L)
+            f[1].record(stream)
+            nl.query_async(s.r_list, CAP)
+            f[2].record(stream)
+            check(qbvh_lj_forward(nl.h, pos4, eps, sig, rc, None, U, F, None, None), "lj")
+            f[3].record(stream)
+            f[3].synchronize()
+            rc_q, _ = nl.query_status()
+            if rc_q != 0:
+                raise RuntimeError(f"query failed: {_lib.QBVHError(rc_q)}")
+            tb.append(f[0].elapsed_time(f[1]))
+            tq.append(f[1].elapsed_time(f[2]))
+            tl.append(f[2].elapsed_time(f[3]))
+        nl.set_option(_lib.QBVH_OPT_FUSED_LJ, 1 if fused else 0)
+        return np.array(tb), np.array(tq), np.array(tl)
+
+    s_build, t_query, t_lj = split_times(max(5, min(args.steps, 20)))
 
     # build and query under each node format (the tuned options otherwise):
     # the paper's 10-bit quantized nodes (Fig. 3b) and FP32 nodes (Fig. 3a)
@@ -325,8 +364,7 @@ def run_ours(args):
     # k computes.
     def step_io(p4, Fo, Uo):
         nl.build(p4, s.L)
-        nl.query_async(s.r_list, CAP)
-        check(qbvh_lj_forward(nl.h, p4, eps, sig, rc, None, Uo, Fo, None, None), "lj")
+        nl.query_lj_async(p4, s.r_list, CAP, eps, sig, rc, None, Uo, Fo, None, None)
 
     copy = torch.cuda.Stream()
     P = [pos4, torch.empty_like(pos4)]
@@ -382,9 +420,20 @@ def run_ours(args):
         hbm = float(peaks["hbm_gbs"]) if peaks else 6800.0
         peak_src = "measured" if peaks else "fallback"
         bytes_q = _alg_bytes(n, total_nbrs)
-        q_avg_s = float(t_query.mean()) * 1e-3
-        achieved = bytes_q / q_avg_s / 1e9
-        step_alg = bytes_q / (float(t_step.mean()) * 1e-3) / 1e9
+        opts_now = autotune.option_names({k: nl.get_option(k) for k in autotune.OPTION_SPACE})
+        q_only = bytes_q / (float(t_query.mean()) * 1e-3) / 1e9
+        nlist_ms = float(s_build.mean()) + float(t_query.mean())
+        if fused:
+            # the traversal also reads nothing more and writes the forces (12 B per particle)
+            bytes_k = bytes_q + 12 * n
+            achieved = bytes_k / (float(t_qlj.mean()) * 1e-3) / 1e9
+            kname = ("query_warp_lj_kernel (traversal + exact leaf test + list write + LJ terms of the "
+                     "accepted pairs; the timed stage includes the FP64 finalize)")
+        else:
+            bytes_k = bytes_q
+            achieved = q_only
+            kname = "query_warp_kernel (traversal + exact leaf test + list write)"
+        step_alg = (bytes_q + 12 * n) / (float(t_step.mean()) * 1e-3) / 1e9
         value = world * n * args.steps / (total_ms * 1e-3)
         out = {
             "metric": METRIC,
@@ -414,28 +463,34 @@ def run_ours(args):
                     nl.get_option(_lib.QBVH_OPT_NODE_FORMAT)],
                 "lj_lanes_per_particle": nl.get_option(_lib.QBVH_OPT_LJ_LANES),
             },
-            "breakdown_ms": {"build": float(t_build.mean()), "query": float(t_query.mean()),
-                             "lj": float(t_lj.mean())},
+            "breakdown_ms": {"build": float(t_build.mean()), "query_lj": float(t_qlj.mean()),
+                             "fused_lj": fused},
+            "split_ms": {"build": float(s_build.mean()), "query": float(t_query.mean()),
+                         "lj": float(t_lj.mean()),
+                         "note": "the same options with the traversal and the LJ list pass as two launches"},
             "node_formats": node_formats,
-            "nlist_particles_per_s": n / (float((t_build + t_query).mean()) * 1e-3),
+            "nlist_particles_per_s": n / (nlist_ms * 1e-3),
             "roofline": {
-                "kernel": "query_kernel (traversal + exact leaf test + list write)",
+                "kernel": kname,
                 "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm,
-                "traffic": _profiled_traffic(autotune.option_names(
-                    {k: nl.get_option(k) for k in autotune.OPTION_SPACE}), n),
+                "traffic": _profiled_traffic(dict(opts_now, fused_lj=int(fused)), n),
                 "peak_source": peak_src,
-                "alg_bytes_per_launch": bytes_q,
+                "alg_bytes_per_launch": bytes_k,
                 "step_frac": step_alg / hbm,
-                "issue": _issue_roofline(autotune.option_names(
-                    {k: nl.get_option(k) for k in autotune.OPTION_SPACE}), n, float(t_query.mean()), clocks),
+                "query_only": {"kernel": "query_warp_kernel (traversal + exact leaf test + list write)",
+                               "query_ms": float(t_query.mean()), "alg_bytes_per_launch": bytes_q,
+                               "achieved": q_only, "frac": q_only / hbm,
+                               "traffic": _profiled_traffic(dict(opts_now, fused_lj=0), n),
+                               "issue": _issue_roofline(dict(opts_now, fused_lj=0), n, float(t_query.mean()),
+                                                        clocks)},
             },
             "e2e": {"value": world * n * e2e_steps / (e2e_ms * 1e-3), "unit": "particles/s",
                     "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 12 * n + 8,
                     "steps": e2e_steps, "ms_per_step": e2e_ms / e2e_steps,
                     "copies": "second stream, double-buffered: step k's D2H and step k+1's H2D overlap step k",
                     "l2": "not flushed; every step writes and reads its 1 GB list, larger than L2"},
-            "gpu_launches": args.steps * KERNELS_PER_STEP,
+            "gpu_launches": args.steps * (KERNELS_PER_STEP_FUSED if fused else KERNELS_PER_STEP),
             "autotune": {"evaluations": tune_evals, "chosen": autotune.option_names(
                 {k: nl.get_option(k) for k in autotune.OPTION_SPACE})},
             "clocks": clocks,
@@ -449,7 +504,7 @@ def run_ours(args):
             out["grid_comparison"] = run_grid_comparison(args, local)
             out["fp64_data"] = run_fp64_comparison(args, local)
             out["false_positives_per_particle"] = run_false_positives(local)
-            out["configs"] = run_configs(args, local, hbm, float((t_build + t_query).mean()), mean_nbrs,
+            out["configs"] = run_configs(args, local, hbm, nlist_ms, mean_nbrs,
                                          out.get("batched"), {k: nl.get_option(k) for k in autotune.OPTION_SPACE})
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(s, samples=1)
@@ -966,6 +1021,8 @@ def main():
     ap.add_argument("--warp-particles", type=int, default=0, help="particles per warp of the walk (0: default)")
     ap.add_argument("--node-format", type=int, default=-1,
                     help="0: 10-bit quantized nodes, 1: FP32 nodes (-1: library default)")
+    ap.add_argument("--fused-lj", type=int, default=-1,
+                    help="LJ terms inside the traversal (1) or a separate list pass (0); -1: autotuned")
     ap.add_argument("--traversal", type=int, default=-1,
                     help="0: one thread per particle, 1: one warp per 32 particles (-1: library default)")
     args = ap.parse_args()

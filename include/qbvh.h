@@ -146,6 +146,14 @@ int qbvh_destroy(qbvh_handle h);
  * and still select the Lennard-Jones parameters.  Takes effect at the next
  * build. */
 #define QBVH_OPT_TYPE_TREES 11
+/* qbvh_query_lj_async: 1 = the traversal evaluates the LJ terms of the pairs
+ * it accepts where it supports that (one system, one type, 32 particles per
+ * warp, exact lists of FP32 data); 0 (default) = the traversal followed by
+ * the separate pass of qbvh_lj_forward.  The summing traversal evaluates the
+ * terms for every pair it tests, about four per listed pair, so at large N
+ * the two passes are faster; the autotuner decides per workload.  Takes
+ * effect at the next call. */
+#define QBVH_OPT_FUSED_LJ 12
 
 int qbvh_set_option(qbvh_handle h, int option, int value);
 int qbvh_get_option(qbvh_handle h, int option, int *value);
@@ -304,6 +312,32 @@ int qbvh_tree_get(qbvh_handle h, const void **nodes, const void **leaves, const 
 int qbvh_lj_forward(qbvh_handle h, const void *pos_dev, const float *eps_dev,
                     const float *sig_dev, const float *r_cut_host, float *e_dev, double *U_dev,
                     float *F_dev, double *dE_dev, double *dS_dev, cudaStream_t stream);
+
+/*
+ * Traversal and Lennard-Jones forward in one call: enqueues qbvh_query_async
+ * (same arguments r_list_host, cap) and the energies, forces and eps/sigma
+ * gradients of qbvh_lj_forward over the list it writes (same arguments and
+ * outputs; pos_dev = the positions of the last build).  This is the step of
+ * a simulation that rebuilds its Verlet list (Sec. 1): the pair energy of
+ * Eq. 1, truncated and shifted at r_cut, is needed for the same pairs the
+ * search has just found.
+ *
+ * With QBVH_OPT_FUSED_LJ = 1, for one system of one type walked 32
+ * particles per warp (the default mapping) with exact lists of FP32 data,
+ * the traversal sums the pair terms of every pair it accepts with
+ * d2 < r_cut^2, from the positions it already holds, and the list is not
+ * read back.  The per-particle sums then run in the walk's order instead of the
+ * row order: the results agree with qbvh_lj_forward to FP32 rounding, not bit
+ * for bit, and are deterministic.  Otherwise the two passes run back to back.
+ * The LJ outputs are valid when qbvh_query_status returns QBVH_OK: after an
+ * overflow the fused sums include the pairs past cap, the separate pass does
+ * not.  No host synchronization.
+ * Errors: NOT_BUILT, INVALID_ARG (as either call), and the enqueue errors of
+ *         qbvh_query_async.
+ */
+int qbvh_query_lj_async(qbvh_handle h, const void *pos_dev, const float *r_list_host, int cap,
+                        const float *eps_dev, const float *sig_dev, const float *r_cut_host, float *e_dev,
+                        double *U_dev, float *F_dev, double *dE_dev, double *dS_dev, cudaStream_t stream);
 
 /*
  * Chain rule for a scalar loss of the per-system energies: with g = dLoss/dU

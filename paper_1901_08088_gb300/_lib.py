@@ -36,6 +36,7 @@ QBVH_OPT_METHOD = 8
 QBVH_OPT_GRID_LANES = 9
 QBVH_OPT_WARP_PARTICLES = 10
 QBVH_OPT_TYPE_TREES = 11
+QBVH_OPT_FUSED_LJ = 12
 
 _lock = threading.Lock()
 _lib = None
@@ -60,6 +61,7 @@ SIGNATURES = {
     "qbvh_query": (I, [P, P, I, I, P]),
     "qbvh_query_async": (I, [P, P, I, P]),
     "qbvh_query_status": (I, [P, PI]),
+    "qbvh_query_lj_async": (I, [P, P, P, I, P, P, P, P, P, P, P, P, P]),
     "nlist_get": (I, [P, PP, PP, PI, PI]),
     "qbvh_tree_get": (I, [P, PP, PP, PP, PP, PP, PI]),
     "qbvh_lj_forward": (I, [P, P, P, P, P, P, P, P, P, P, P]),

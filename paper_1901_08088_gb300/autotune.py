@@ -33,9 +33,11 @@ OPTION_SPACE = {
 }
 
 # options a caller adds to the search where they apply: one tree per system
-# only when every type pair has the same list radius
+# only when every type pair has the same list radius; the LJ terms inside the
+# traversal only for a step that evaluates LJ over the list it builds
 OPTIONAL_SPACE = {
     _lib.QBVH_OPT_TYPE_TREES: [1, 0],
+    _lib.QBVH_OPT_FUSED_LJ: [1, 0],
 }
 
 DEFAULTS = {
@@ -46,6 +48,7 @@ DEFAULTS = {
     _lib.QBVH_OPT_QUERY_BLOCK: 128,
     _lib.QBVH_OPT_LJ_LANES: 2,
     _lib.QBVH_OPT_TYPE_TREES: 1,
+    _lib.QBVH_OPT_FUSED_LJ: 0,
 }
 
 _NAMES = {
@@ -59,6 +62,7 @@ _NAMES = {
     _lib.QBVH_OPT_METHOD: "method",
     _lib.QBVH_OPT_LJ_ZORDER: "lj_zorder",
     _lib.QBVH_OPT_TYPE_TREES: "type_trees",
+    _lib.QBVH_OPT_FUSED_LJ: "fused_lj",
 }
 
 

@@ -72,6 +72,7 @@ struct qbvh_ctx {
     int method = 0;        // 0: quantized BVH, 1: uniform grid comparator
     int grid_tpp = 8;      // lanes per particle of the grid traversal
     int type_trees = 1;    // 1: one tree per (system, type); 0: one tree per system
+    int fused_lj = 0;      // qbvh_query_lj_async: LJ terms inside the traversal where supported
     int built_method = 0;
     const void *grid_pos = nullptr;   // positions recorded by a grid-method build
     int built_fmt = 0;     // node format of the last build
@@ -411,7 +412,25 @@ int grid_enqueue(qbvh_ctx *h, const float *r_list, const float *rl2, int cap, cu
     return cuda_status();
 }
 
-int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s)
+// LJ outputs requested with the traversal (qbvh_query_lj_async)
+struct QueryLJ {
+    const void *pos;
+    const float *eps, *sig, *r_cut;
+    float *e;
+    double *U;
+    float *F;
+    double *dE, *dS;
+};
+
+// The traversal sums the LJ terms itself for one system of one type walked
+// one particle per lane (exact lists of FP32 data, quantized BVH).
+bool fused_lj_ok(const qbvh_ctx *h)
+{
+    return h->fused_lj && h->built_method == 0 && !h->f64 && !h->candidates && h->traversal == 1 &&
+           h->warp_particles == 32 && h->n_sys == 1 && h->n_types == 1 && h->n > 0;
+}
+
+int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s, const QueryLJ *lj = nullptr)
 {
     NvtxRange range("qbvh_query");
     if (!h) return QBVH_ERR_INVALID_ARG;
@@ -510,7 +529,23 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
     q.f64 = h->f64 ? 1 : 0;
     q.leaves64 = h->f64 ? reinterpret_cast<const double4_32a *>(h->leaves64.p) : nullptr;
     q.L64 = h->L64;
-    launch_query(q, s);
+    if (lj && fused_lj_ok(h)) {
+        const int nb = query_lj_blocks(h->n, h->query_block);
+        rc = ensure(h, h->lj_partials, (size_t)nb * 3 * 8);
+        if (rc) return rc;
+        const float rc_ = lj->r_cut[0];
+        q.lj = 1;
+        q.lj_eps = lj->eps;
+        q.lj_sig = lj->sig;
+        q.lj_rc2 = rc_ * rc_;
+        q.lj_e = lj->e;
+        q.lj_F = lj->F;
+        q.lj_partials = reinterpret_cast<double *>(h->lj_partials.p);
+        launch_query_lj(q, s);
+        launch_lj_finalize_one(q.lj_partials, nb, lj->U, lj->dE, lj->dS, s);
+    } else {
+        launch_query(q, s);
+    }
     if (cudaMemcpyAsync(h->h_status, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return QBVH_ERR_CUDA;
     rc = cuda_status();
@@ -644,6 +679,10 @@ int qbvh_set_option(qbvh_handle h, int option, int value)
         if (value != 0 && value != 1) return QBVH_ERR_INVALID_ARG;
         h->type_trees = value;
         return QBVH_OK;
+    case QBVH_OPT_FUSED_LJ:
+        if (value != 0 && value != 1) return QBVH_ERR_INVALID_ARG;
+        h->fused_lj = value;
+        return QBVH_OK;
     default: return QBVH_ERR_INVALID_ARG;
     }
 }
@@ -663,6 +702,7 @@ int qbvh_get_option(qbvh_handle h, int option, int *value)
     case QBVH_OPT_METHOD: *value = h->method; return QBVH_OK;
     case QBVH_OPT_GRID_LANES: *value = h->grid_tpp; return QBVH_OK;
     case QBVH_OPT_TYPE_TREES: *value = h->type_trees; return QBVH_OK;
+    case QBVH_OPT_FUSED_LJ: *value = h->fused_lj; return QBVH_OK;
     default: return QBVH_ERR_INVALID_ARG;
     }
 }
@@ -691,6 +731,26 @@ int qbvh_build_batched(qbvh_handle h, const void *pos_dev, int n_total, int n_sy
 int qbvh_query_async(qbvh_handle h, const float *r_list_host, int cap, cudaStream_t stream)
 {
     return query_enqueue(h, r_list_host, cap, stream);
+}
+
+int qbvh_query_lj_async(qbvh_handle h, const void *pos_dev, const float *r_list_host, int cap,
+                        const float *eps_dev, const float *sig_dev, const float *r_cut_host, float *e_dev,
+                        double *U_dev, float *F_dev, double *dE_dev, double *dS_dev, cudaStream_t stream)
+{
+    if (!h) return QBVH_ERR_INVALID_ARG;
+    if (!h->built) return QBVH_ERR_NOT_BUILT;
+    if (!r_list_host || !eps_dev || !sig_dev || !r_cut_host || !U_dev) return QBVH_ERR_INVALID_ARG;
+    if (h->n > 0 && (!pos_dev || ((uintptr_t)pos_dev & 15u))) return QBVH_ERR_INVALID_ARG;
+    const int T = h->n_types;
+    for (int p = 0; p < T * T; ++p) {
+        const float rc = r_cut_host[p];
+        if (!(rc > 0.f) || !isfinite(rc) || rc > r_list_host[p]) return QBVH_ERR_INVALID_ARG;
+    }
+    const QueryLJ lj{pos_dev, eps_dev, sig_dev, r_cut_host, e_dev, U_dev, F_dev, dE_dev, dS_dev};
+    const bool fused = fused_lj_ok(h);
+    int rc = query_enqueue(h, r_list_host, cap, stream, &lj);
+    if (rc || fused) return rc;
+    return qbvh_lj_forward(h, pos_dev, eps_dev, sig_dev, r_cut_host, e_dev, U_dev, F_dev, dE_dev, dS_dev, stream);
 }
 
 int qbvh_query_status(qbvh_handle h, int *max_count)

@@ -175,13 +175,17 @@ lj_forward_kernel(const __grid_constant__ LJArgs a)
 // independent, so they are in flight together), then a fixed-order tree
 // adds the 1024 run sums: the same order on every call.
 constexpr int kFinThreads = 1024;
+// Without a block table (sys_blk_start == nullptr) one system owns records
+// [0, n_blocks).
 __global__ void __launch_bounds__(kFinThreads) lj_finalize_kernel(const double *partials, const int *sys_blk_start,
-                                                                  int np, int T, double *U, double *dE, double *dS)
+                                                                  int np, int T, double *U, double *dE, double *dS,
+                                                                  int n_blocks = 0)
 {
     __shared__ double s[kFinThreads];
     const int sys = blockIdx.x;
     const int t = threadIdx.x;
-    const int b0 = sys_blk_start[sys], b1 = sys_blk_start[sys + 1];
+    const int b0 = sys_blk_start ? sys_blk_start[sys] : 0;
+    const int b1 = sys_blk_start ? sys_blk_start[sys + 1] : n_blocks;
     const int run = (b1 - b0 + kFinThreads - 1) / kFinThreads;
     const int r0 = b0 + t * run, r1 = min(r0 + run, b1);
     for (int q = 0; q < np; ++q) {
@@ -273,6 +277,12 @@ void launch_lj_forward(const LJArgs &a, cudaStream_t s)
     }
     const int T = a.n_types;
     lj_finalize_kernel<<<a.n_sys, kFinThreads, 0, s>>>(a.partials, a.sys_blk_start, 1 + 2 * T * T, T, a.U, a.dE, a.dS);
+}
+
+void launch_lj_finalize_one(const double *partials, int n_blocks, double *U, double *dE, double *dS,
+                            cudaStream_t s)
+{
+    lj_finalize_kernel<<<1, kFinThreads, 0, s>>>(partials, nullptr, 3, 1, U, dE, dS, n_blocks);
 }
 
 void launch_lj_backward(const double *g, const float *F, const double *dE, const double *dS, float *gpos,

@@ -82,6 +82,12 @@ __device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c)
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
+__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 
 
 // ---- Lennard-Jones pair terms (Eq. 1, truncated and shifted) -------------
@@ -417,9 +423,23 @@ struct QueryArgs {
     float rl2[64];         // fl(r * r)
     float rs[64];          // padded search radius (rounded up)
     float rs2[64];         // rs^2 rounded up
+    // Lennard-Jones terms of the accepted pairs, evaluated during the walk
+    // (one system, one type; lj = 1): eps/sig [1] on the device, fl(r_c^2),
+    // per-particle outputs by original index and one FP64 record per block
+    int lj;
+    const float *lj_eps, *lj_sig;
+    float lj_rc2;
+    float *lj_e, *lj_F;
+    double *lj_partials;
 };
 
 void launch_query(const QueryArgs &a, cudaStream_t s);
+
+// Traversal with the Lennard-Jones terms of the accepted pairs (a.lj = 1):
+// one system, one type, one particle per lane, exact lists of FP32 data.
+// query_lj_blocks = its block count (one FP64 record per block).
+int query_lj_blocks(int n, int block);
+void launch_query_lj(const QueryArgs &a, cudaStream_t s);
 
 // ---- uniform grid comparator (grid.cu) ----------------------------------
 struct GridArgs {
@@ -475,6 +495,11 @@ struct LJArgs {
 };
 
 void launch_lj_forward(const LJArgs &a, cudaStream_t s);
+
+// fixed-order FP64 sums of one system's n_blocks records of 3 values
+// (U, dU/deps, dU/dsig of one type), as written by the fused traversal
+void launch_lj_finalize_one(const double *partials, int n_blocks, double *U, double *dE, double *dS,
+                            cudaStream_t s);
 
 void launch_lj_backward(const double *g, const float *F, const double *dE, const double *dS,
                         float *gpos, float *geps, float *gsig, int n, int n_sys, int n_types,

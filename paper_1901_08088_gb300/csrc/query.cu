@@ -358,6 +358,9 @@ struct Query {
     float rl2;
     float rl2_lo, rl2_hi; // double-precision data: band of the FP32 test around rl2
     int pair;             // double-precision data: type pair of the current tree
+    // Lennard-Jones value of an image pair (fused option): per axis the
+    // difference fl(fl(xj - v1) - v2), the once-rounded x_j - x_i - n L
+    float vx1, vy1, vz1, vx2, vy2, vz2;
 };
 
 // d2 of the exact test (see the header comment) for leaf position q.
@@ -881,9 +884,90 @@ __device__ __forceinline__ void packet_box(const Query &c, bool on, BundleStage 
     __syncwarp();
 }
 
-template <bool SHIFT, bool SELF>
+// ---- Lennard-Jones terms of the accepted pairs (fused option) ------------
+// With QueryArgs::lj set (one system, one type) the walk evaluates the
+// truncated and shifted pair energy of Eq. 1 for every pair it accepts with
+// d2 < fl(r_c^2), from the positions it already holds, so that the list is
+// not read back by a second pass.  Per lane (one particle) it sums, two
+// survivors per packed step, with s = (sig^2 / r^2)^3:
+//   t = sum (s^2 - s),  q = sum (2 s^2 - s),  f = sum (2 s^2 - s) / r^2 v,
+//   n = number of interacting pairs,
+// and at the end forms e_i = eps (4 t - phic n), F_i = -24 eps f,
+// dU/deps = 1/2 sum_i (4 t - phic n), dU/dsig = 1/2 sum_i (24 eps / sig) (q - dsc n)
+// (the same terms as the list pass, summed in another order).  Membership
+// is the list's pinned d2 < fl(r_c^2); the value takes v = x_j - x_i - n L
+// rounded once, as the list pass does.  A pair that does not interact gets
+// r^2 = 1e30: its s underflows to zero and every term vanishes.
+struct LJAcc {
+    f32x2 t, q, fx, fy, fz;
+    float n;
+};
+
+__device__ __forceinline__ float lj_rcp_fast(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void lj_terms2(LJAcc &A, float sig2, bool l0, bool l1, float r0, float r1, f32x2 vx,
+                                          f32x2 vy, f32x2 vz)
+{
+    const f32x2 inv = f2_pack(lj_rcp_fast(l0 ? r0 : 1e30f), lj_rcp_fast(l1 ? r1 : 1e30f));
+    const f32x2 s2 = f2_mul(f2_pack(sig2, sig2), inv);
+    const f32x2 s4 = f2_mul(s2, s2);
+    const f32x2 s6 = f2_mul(s4, s2);
+    const f32x2 s12 = f2_mul(s6, s6);
+    A.t = f2_add(A.t, f2_sub(s12, s6));
+    const f32x2 q = f2_sub(f2_add(s12, s12), s6);
+    A.q = f2_add(A.q, q);
+    const f32x2 w = f2_mul(q, inv);
+    A.fx = f2_fma(w, vx, A.fx);
+    A.fy = f2_fma(w, vy, A.fy);
+    A.fz = f2_fma(w, vz, A.fz);
+    A.n += (l0 ? 1.f : 0.f) + (l1 ? 1.f : 0.f);
+}
+
+// value offsets of the current image (see Query): n > 0: fl(fl(xj - L) - xi);
+// n < 0: fl(xj - fl(xi - L)) (fl(xi + n L) is the image centre); n = 0: fl(xj - xi)
+__device__ __forceinline__ void set_lj_value(Query &c, float L)
+{
+    c.vx1 = c.nLx > 0.f ? L : c.px;
+    c.vy1 = c.nLy > 0.f ? L : c.py;
+    c.vz1 = c.nLz > 0.f ? L : c.pz;
+    c.vx2 = c.nLx > 0.f ? c.xi : 0.f;
+    c.vy2 = c.nLy > 0.f ? c.yi : 0.f;
+    c.vz2 = c.nLz > 0.f ? c.zi : 0.f;
+}
+
+// LJ terms of one pair already tested (scalar: odd survivors, single leaves)
+template <bool SHIFT>
+__device__ __forceinline__ void lj_single(LJAcc &A, const Query &c, float sig2, float rc2, bool acc, float d2,
+                                          float4 q)
+{
+    float vx, vy, vz, r2;
+    if (SHIFT) {
+        vx = __fsub_rn(__fsub_rn(q.x, c.vx1), c.vx2);
+        vy = __fsub_rn(__fsub_rn(q.y, c.vy1), c.vy2);
+        vz = __fsub_rn(__fsub_rn(q.z, c.vz1), c.vz2);
+        r2 = __fadd_rn(__fadd_rn(__fmul_rn(vx, vx), __fmul_rn(vy, vy)), __fmul_rn(vz, vz));
+    } else {
+        vx = __fsub_rn(q.x, c.xi);
+        vy = __fsub_rn(q.y, c.yi);
+        vz = __fsub_rn(q.z, c.zi);
+        r2 = d2;
+    }
+    lj_terms2(A, sig2, acc && d2 < rc2, false, r2, 1e30f, f2_pack(vx, 0.f), f2_pack(vy, 0.f), f2_pack(vz, 0.f));
+}
+
+struct LJCtx {
+    LJAcc *acc;   // nullptr: no LJ terms
+    float sig2, rc2;
+};
+
+template <bool SHIFT, bool SELF, bool LJ = false>
 __device__ __forceinline__ void survivor_pair(const Query &c, Row &out, int t, bool on, const BundleStage *st,
-                                              bool staged)
+                                              bool staged, const LJCtx &lj = LJCtx{})
 {
     const f32x2 X = *reinterpret_cast<const f32x2 *>(st->x + t);
     const f32x2 Y = *reinterpret_cast<const f32x2 *>(st->y + t);
@@ -904,6 +988,22 @@ __device__ __forceinline__ void survivor_pair(const Query &c, Row &out, int t, b
     const float d1 = __fadd_rn(__fadd_rn(sx1, sy1), sz1);
     const bool a0 = on && d0 < c.rl2 && (!SELF || id.x != c.self_id);
     const bool a1 = on && d1 < c.rl2 && (!SELF || id.y != c.self_id);
+    if (LJ) {
+        f32x2 vx = dx, vy = dy, vz = dz;
+        float r0 = d0, r1 = d1;
+        if (SHIFT) {
+            vx = f2_sub(f2_sub(X, f2_pack(c.vx1, c.vx1)), f2_pack(c.vx2, c.vx2));
+            vy = f2_sub(f2_sub(Y, f2_pack(c.vy1, c.vy1)), f2_pack(c.vy2, c.vy2));
+            vz = f2_sub(f2_sub(Z, f2_pack(c.vz1, c.vz1)), f2_pack(c.vz2, c.vz2));
+            float ux0, ux1, uy0, uy1, uz0, uz1;
+            f2_unpack(f2_mul(vx, vx), ux0, ux1);
+            f2_unpack(f2_mul(vy, vy), uy0, uy1);
+            f2_unpack(f2_mul(vz, vz), uz0, uz1);
+            r0 = __fadd_rn(__fadd_rn(ux0, uy0), uz0);
+            r1 = __fadd_rn(__fadd_rn(ux1, uy1), uz1);
+        }
+        lj_terms2(*lj.acc, lj.sig2, a0 && d0 < lj.rc2, a1 && d1 < lj.rc2, r0, r1, vx, vy, vz);
+    }
     if (staged) {
         out.stage(id.x, a0);
         out.stage(id.y, a1);
@@ -921,25 +1021,28 @@ __device__ __forceinline__ void survivor_pair(const Query &c, Row &out, int t, b
 // of the N = 2M list differed at d = r_list.  Scalar add.rn is not contracted.)
 // With row staging the accepted entries are staged without a branch and the
 // completed sectors written once per 8 survivors and at the end.
-template <bool SHIFT, bool SELF>
-__device__ __forceinline__ void survivors_loop(const Query &c, Row &out, int s, bool on, const BundleStage *st)
+template <bool SHIFT, bool SELF, bool LJ = false>
+__device__ __forceinline__ void survivors_loop(const Query &c, Row &out, int s, bool on, const BundleStage *st,
+                                               const LJCtx &lj = LJCtx{})
 {
     const bool staged = out.ring != nullptr;
     int t = 0;
     if (staged) {
         for (; t + 8 <= s; t += 8) {
-            survivor_pair<SHIFT, SELF>(c, out, t, on, st, true);
-            survivor_pair<SHIFT, SELF>(c, out, t + 2, on, st, true);
-            survivor_pair<SHIFT, SELF>(c, out, t + 4, on, st, true);
-            survivor_pair<SHIFT, SELF>(c, out, t + 6, on, st, true);
+            survivor_pair<SHIFT, SELF, LJ>(c, out, t, on, st, true, lj);
+            survivor_pair<SHIFT, SELF, LJ>(c, out, t + 2, on, st, true, lj);
+            survivor_pair<SHIFT, SELF, LJ>(c, out, t + 4, on, st, true, lj);
+            survivor_pair<SHIFT, SELF, LJ>(c, out, t + 6, on, st, true, lj);
             out.check();
         }
     }
-    for (; t + 1 < s; t += 2) survivor_pair<SHIFT, SELF>(c, out, t, on, st, staged);
+    for (; t + 1 < s; t += 2) survivor_pair<SHIFT, SELF, LJ>(c, out, t, on, st, staged, lj);
     if (t < s) {
         const float4 q = make_float4(st->x[t], st->y[t], st->z[t], 0.f);
         const int id = st->id[t];
-        const bool acc = on && exact_d2<SHIFT>(c, q) < c.rl2 && (!SELF || id != c.self_id);
+        const float d2 = exact_d2<SHIFT>(c, q);
+        const bool acc = on && d2 < c.rl2 && (!SELF || id != c.self_id);
+        if (LJ) lj_single<SHIFT>(*lj.acc, c, lj.sig2, lj.rc2, acc, d2, q);
         if (staged) out.stage(id, acc);
         else if (acc) out.push(id);
     }
@@ -991,9 +1094,10 @@ __device__ __forceinline__ void survivors_spread(const QueryArgs &a, const Query
 
 // A chunk of cnt <= 32 leaves starting at `first` of a bundle overlapped by
 // the lanes in hm (warp-uniform).  Every lane of the warp calls this together.
-template <bool SHIFT, bool SELF>
+template <bool SHIFT, bool SELF, bool LJ = false>
 __device__ __forceinline__ void bundle_chunk(const QueryArgs &a, const Query &c, Row &out, int first, int cnt,
-                                             unsigned hm, bool on, float rs2, BundleStage *st)
+                                             unsigned hm, bool on, float rs2, BundleStage *st,
+                                             const LJCtx &lj = LJCtx{})
 {
     const int lane = threadIdx.x & 31;
     const bool v = lane < cnt;
@@ -1022,22 +1126,23 @@ __device__ __forceinline__ void bundle_chunk(const QueryArgs &a, const Query &c,
     const int m = __popc(hm);
     const int wsh = s <= 8 ? 3 : (s <= 16 ? 4 : 5);
     const int kk = 32 >> wsh;
-    const bool spread = QBVH_FILTER_SPREAD && !QBVH_ROW_STAGING && m <= QBVH_FILTER_SPREAD_MAX &&
+    const bool spread = QBVH_FILTER_SPREAD && !QBVH_ROW_STAGING && !LJ && m <= QBVH_FILTER_SPREAD_MAX &&
                         (QBVH_SPREAD_COST + 3 * kk) * ((m + kk - 1) / kk) < QBVH_LOOP_COST * s;
     if (spread && ((hm >> lane) & 1u)) st->owner[__popc(hm & lt)] = lane;
     __syncwarp();
     if (spread) survivors_spread<SHIFT, SELF>(a, c, out, s, m, wsh, hm, st);
-    else survivors_loop<SHIFT, SELF>(c, out, s, on, st);
+    else survivors_loop<SHIFT, SELF, LJ>(c, out, s, on, st, lj);
     __syncwarp();   // the next bundle rewrites the stage
 }
 
 // A bundle of cnt <= 64 leaves, in chunks of 32 (one leaf per lane).
-template <bool SHIFT, bool SELF>
+template <bool SHIFT, bool SELF, bool LJ = false>
 __device__ __forceinline__ void bundle_filtered(const QueryArgs &a, const Query &c, Row &out, int first, int cnt,
-                                                unsigned hm, bool on, float rs2, BundleStage *st)
+                                                unsigned hm, bool on, float rs2, BundleStage *st,
+                                                const LJCtx &lj = LJCtx{})
 {
     for (int base = 0; base < cnt; base += 32)
-        bundle_chunk<SHIFT, SELF>(a, c, out, first + base, min(32, cnt - base), hm, on, rs2, st);
+        bundle_chunk<SHIFT, SELF, LJ>(a, c, out, first + base, min(32, cnt - base), hm, on, rs2, st, lj);
 }
 
 // bundle leaves tested two per step (two loads in flight; measured 2.25 ->
@@ -1074,11 +1179,13 @@ __device__ __forceinline__ void bundle_loop(const QueryArgs &a, const Query &c, 
 #endif
 // ---- one warp per 32 consecutive Z-order particles ----------------------
 // The warp-uniform rope walk of one tree under one periodic image.
-template <bool CAND, int FMT, bool SHIFT, int W, bool F64>
+template <bool CAND, int FMT, bool SHIFT, int W, bool F64, bool LJ = false>
 __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Row &out, const SegInfo &g,
                                           const Frame &f, int root, int last, bool on, float rs2, int wsub,
-                                          unsigned same, BundleStage *st = nullptr, float rs = 0.f)
+                                          unsigned same, BundleStage *st = nullptr, float rs = 0.f,
+                                          const LJCtx &lj = LJCtx{})
 {
+    static_assert(!LJ || (stage_on(W, CAND, F64) && !CAND && !F64 && W == 1), "LJ terms need the filtered walk");
     // bundles filtered against the warp's box (one particle per lane, exact lists of FP32 data)
     constexpr bool FILTER = stage_on(W, CAND, F64);
     // 10-bit nodes tested in the integer domain on the same walks
@@ -1121,8 +1228,8 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                     const bool self_here =
                         !SHIFT && __any_sync(FULL, (unsigned)(c.self - j) <= (unsigned)(l - j));
                     if (FILTER && l - j < 64) {
-                        if (self_here) bundle_filtered<SHIFT, true>(a, c, out, j, l - j + 1, hm, on, rs2, st);
-                        else bundle_filtered<SHIFT, false>(a, c, out, j, l - j + 1, hm, on, rs2, st);
+                        if (self_here) bundle_filtered<SHIFT, true, LJ>(a, c, out, j, l - j + 1, hm, on, rs2, st, lj);
+                        else bundle_filtered<SHIFT, false, LJ>(a, c, out, j, l - j + 1, hm, on, rs2, st, lj);
                     } else if (W == 1 && !CAND && l - j < 32 && __popc(hm) <= QBVH_SPREAD_MAX) {
                         if (self_here) bundle_spread<SHIFT, F64, true>(a, c, out, j, l - j + 1, hm);
                         else bundle_spread<SHIFT, F64, false>(a, c, out, j, l - j + 1, hm);
@@ -1153,7 +1260,12 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
         } else {
             const int j = ~node;
             const float4 q = tree_ld(a.leaves + j);
-            if (W == 1) {
+            if (LJ) {
+                const float d2 = exact_d2<SHIFT>(c, q);
+                const bool acc = on && d2 < c.rl2 && j != c.self;
+                lj_single<SHIFT>(*lj.acc, c, lj.sig2, lj.rc2, acc, d2, q);
+                if (acc) out.push(__float_as_int(q.w) & 0x7FFFFFFF);
+            } else if (W == 1) {
                 if (on) test_leaf<CAND, SHIFT, F64, true, FMT>(a, c, out, j, q, f, rs2);
             } else {
                 const bool acc = wsub == 0 && on && leaf_accepts<CAND, SHIFT, F64, FMT>(a, c, j, q, f, rs2);
@@ -1290,9 +1402,40 @@ __host__ __device__ constexpr unsigned same_lanes(int W)
     return m;
 }
 
-template <bool WIDE, bool CAND, int FMT, int W, bool ONE, int PHASE, bool F64 = false>
-__global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ QueryArgs a)
+// Register cap of the traversal that also sums the LJ terms: its eleven
+// accumulators do not fit under the plain walk's 32 registers.
+#ifndef QBVH_QUERY_LJ_MIN_BLOCKS
+#define QBVH_QUERY_LJ_MIN_BLOCKS 5
+#endif
+
+// FP64 record of one block: the fixed-order sum over its lanes of U, dU/deps
+// and dU/dsig (the same three values the list pass writes per block)
+__device__ __forceinline__ void lj_block_record(const QueryArgs &a, double v0, double v1, double v2)
 {
+    __shared__ double s_red[8][3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_down_sync(FULL, v0, o);
+        v1 += __shfl_down_sync(FULL, v1, o);
+        v2 += __shfl_down_sync(FULL, v2, o);
+    }
+    if (lane == 0) {
+        s_red[warp][0] = v0;
+        s_red[warp][1] = v1;
+        s_red[warp][2] = v2;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double x = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += s_red[w][threadIdx.x];
+        a.lj_partials[(size_t)blockIdx.x * 3 + threadIdx.x] = x;
+    }
+}
+
+template <bool WIDE, bool CAND, int FMT, int W, bool ONE, int PHASE, bool F64, bool LJ>
+__device__ __forceinline__ void warp_query(const QueryArgs &a)
+{
+    static_assert(!LJ || (ONE && W == 1 && !CAND && !F64 && PHASE == 2), "LJ terms: one tree, filtered walk");
     constexpr int G = 32 / W;
     // sparse trees (above) exist for single-system builds with several types
     constexpr bool SPARSE = QBVH_SPARSE_TREES && !WIDE && !ONE && !CAND && !F64 && PHASE == 2;
@@ -1349,6 +1492,16 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
     out.base = 0;
     bool walked = PHASE != 1;
     bool elsewhere = false;   // particle of a sparse tree: walked by the leading blocks
+    LJAcc acc;
+    LJCtx lj;
+    if (LJ) {
+        acc.t = acc.q = acc.fx = acc.fy = acc.fz = f2_pack(0.f, 0.f);
+        acc.n = 0.f;
+        const float sg = __ldg(a.lj_sig);
+        lj.acc = &acc;
+        lj.sig2 = sg * sg;
+        lj.rc2 = a.lj_rc2;
+    }
     const int T = ONE ? 1 : a.n_types;
     // the warp's particles may belong to several trees (segment boundaries):
     // take one segment value at a time
@@ -1394,22 +1547,63 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
                 const int img = __ffs(mask) - 1;
                 mask &= mask - 1u;
                 set_image(c, img, L);
+                if (LJ) set_lj_value(c, L);
                 const bool on = (mine >> img) & 1u;
                 if (PHASE == 2 && img == 13)
-                    warp_walk<CAND, FMT, false, W, F64>(a, c, out, g, f, root, last, on, rs2, wsub, same, st, rs);
+                    warp_walk<CAND, FMT, false, W, F64, LJ>(a, c, out, g, f, root, last, on, rs2, wsub, same, st,
+                                                            rs, lj);
                 else
-                    warp_walk<CAND, FMT, true, W, F64>(a, c, out, g, f, root, last, on, rs2, wsub, same, st, rs);
+                    warp_walk<CAND, FMT, true, W, F64, LJ>(a, c, out, g, f, root, last, on, rs2, wsub, same, st,
+                                                           rs, lj);
             }
         }
     }
     if (!walked) return;   // phase 1, no image to add for this warp: counts stay
     if (RING && active && !elsewhere) out.drain();
-    if (active && wsub == 0 && !elsewhere) {
-        // the row index again (not kept live across the walk)
-        int io = __float_as_int(__ldg(a.leaves + s).w) & 0x7FFFFFFF;
-        a.counts[io < a.n ? io : s] = out.count;
+    // the row index again (not kept live across the walk)
+    int io = 0;
+    if (active) {
+        io = __float_as_int(__ldg(a.leaves + s).w) & 0x7FFFFFFF;
+        io = io < a.n ? io : s;
     }
+    if (active && wsub == 0 && !elsewhere) a.counts[io] = out.count;
     warp_max_count(active && !elsewhere ? out.count : 0, a.status);
+    if (LJ) {
+        float t0, t1, q0, q1, x0, x1, y0, y1, z0, z1;
+        f2_unpack(acc.t, t0, t1);
+        f2_unpack(acc.q, q0, q1);
+        f2_unpack(acc.fx, x0, x1);
+        f2_unpack(acc.fy, y0, y1);
+        f2_unpack(acc.fz, z0, z1);
+        const float eps = __ldg(a.lj_eps), sig = __ldg(a.lj_sig);
+        const LJParams p = lj_params(eps, sig, a.lj_rc2);
+        const float uE = __fsub_rn(4.f * __fadd_rn(t0, t1), p.phic * acc.n);   // sum of u / eps
+        const float e = eps * uE;
+        const float c24 = -24.f * eps;
+        if (active) {
+            if (a.lj_e) a.lj_e[io] = 0.5f * e;
+            if (a.lj_F) {
+                a.lj_F[3 * (size_t)io] = c24 * __fadd_rn(x0, x1);
+                a.lj_F[3 * (size_t)io + 1] = c24 * __fadd_rn(y0, y1);
+                a.lj_F[3 * (size_t)io + 2] = c24 * __fadd_rn(z0, z1);
+            }
+        }
+        const float gs = (24.f * eps / sig) * __fsub_rn(__fadd_rn(q0, q1), p.dsc * acc.n);
+        lj_block_record(a, 0.5 * (double)e, 0.5 * (double)uE, 0.5 * (double)gs);
+    }
+}
+
+template <bool WIDE, bool CAND, int FMT, int W, bool ONE, int PHASE, bool F64 = false>
+__global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ QueryArgs a)
+{
+    warp_query<WIDE, CAND, FMT, W, ONE, PHASE, F64, false>(a);
+}
+
+// the walk of one system of one type that also sums the LJ terms of its pairs
+template <int FMT>
+__global__ void __launch_bounds__(256, QBVH_QUERY_LJ_MIN_BLOCKS) query_warp_lj_kernel(const __grid_constant__ QueryArgs a)
+{
+    warp_query<false, false, FMT, 1, true, 2, false, true>(a);
 }
 
 }  // namespace
@@ -1509,6 +1703,23 @@ static void launch_f64(const QueryArgs &a, cudaStream_t s)
     const size_t sm = stage_bytes(b, stage_on(1, false, true));
     if (a.n_types == 1) query_warp_kernel<false, false, FMT, 1, true, 2, true><<<grid, b, sm, s>>>(a);
     else query_warp_kernel<false, false, FMT, 1, false, 2, true><<<grid, b, sm, s>>>(a);
+}
+
+int query_lj_blocks(int n, int block)
+{
+    const long long threads = (long long)((n + 31) / 32) * 32;
+    return (int)((threads + block - 1) / block);
+}
+
+void launch_query_lj(const QueryArgs &a, cudaStream_t s)
+{
+    if (a.n == 0) return;
+    const int b = a.block;
+    const int grid = query_lj_blocks(a.n, b);
+    const size_t sm = stage_bytes(b, true);
+    if (a.node_fmt == 0) query_warp_lj_kernel<0><<<grid, b, sm, s>>>(a);
+    else if (a.node_fmt == 1) query_warp_lj_kernel<1><<<grid, b, sm, s>>>(a);
+    else query_warp_lj_kernel<2><<<grid, b, sm, s>>>(a);
 }
 
 void launch_query(const QueryArgs &a, cudaStream_t s)

@@ -20,6 +20,7 @@ __all__ = [
     "QBVHError", "NeighborList",
     "qbvh_create", "qbvh_destroy", "qbvh_set_option", "qbvh_get_option",
     "qbvh_build", "qbvh_build_f64", "qbvh_build_batched", "qbvh_query", "qbvh_query_async", "qbvh_query_status",
+    "qbvh_query_lj_async",
     "nlist_get", "qbvh_tree_get", "qbvh_lj_forward", "qbvh_lj_backward", "qbvh_pack_positions",
     "qbvh_lj_forward_noalloc", "qbvh_selftest_wait_timeout", "qbvh_strerror",
 ]
@@ -123,6 +124,16 @@ def qbvh_query(h: int, r_list, n_types: int, cap: int = 256, max_retries: int = 
 def qbvh_query_async(h: int, r_list, n_types: int, cap: int, stream=None) -> int:
     r = _rl(r_list, n_types)
     return lib().qbvh_query_async(h, r.ctypes.data_as(C.c_void_p), int(cap), _stream_ptr(stream))
+
+
+def qbvh_query_lj_async(h: int, pos4, r_list, n_types: int, cap: int, eps, sig, r_cut_host, e, U, F, dE, dS,
+                        stream=None) -> int:
+    """Traversal + LJ forward over the list it writes (fused where the library supports it)."""
+    r = _rl(r_list, n_types)
+    rc = np.ascontiguousarray(np.broadcast_to(np.asarray(r_cut_host, np.float32), (n_types, n_types)))
+    return lib().qbvh_query_lj_async(h, _ptr(pos4), r.ctypes.data_as(C.c_void_p), int(cap), _ptr(eps), _ptr(sig),
+                                     rc.ctypes.data_as(C.c_void_p), _ptr(e), _ptr(U), _ptr(F), _ptr(dE), _ptr(dS),
+                                     _stream_ptr(stream))
 
 
 def qbvh_query_status(h: int):
@@ -247,6 +258,13 @@ class NeighborList:
 
     def query_async(self, r_list, cap: int, stream=None):
         check(qbvh_query_async(self.h, r_list, self.n_types, cap, stream), "qbvh_query_async")
+
+    def query_lj_async(self, pos4, r_list, cap: int, eps, sig, r_cut, e=None, U=None, F=None, dE=None, dS=None,
+                       stream=None):
+        """Enqueue the traversal and the LJ energies/forces over its list; read
+        the outcome with ``query_status`` after the stream completes."""
+        check(qbvh_query_lj_async(self.h, pos4, r_list, self.n_types, cap, eps, sig, r_cut, e, U, F, dE, dS,
+                                  stream), "qbvh_query_lj_async")
 
     def query_status(self):
         return qbvh_query_status(self.h)

@@ -61,6 +61,7 @@ def test_null_and_invalid_arguments_are_rejected_on_host(lib):
     assert lib.qbvh_build(None, None, 0, 1.0, 1, None) == E
     assert lib.qbvh_query(None, None, 8, 0, None) == E
     assert lib.qbvh_query_status(None, None) == E
+    assert lib.qbvh_query_lj_async(None, None, None, 8, None, None, None, None, None, None, None, None, None) == E
     assert lib.nlist_get(None, None, None, None, None) == E
     assert lib.qbvh_set_option(None, 1, 4) == E
     assert lib.qbvh_pack_positions(None, None, -1, None, None) == E
