@@ -27,8 +27,8 @@ def _rel(a, b):
 
 
 def _fused(s, E, S, rc, cap=256, fused=1, **opts):
-    # fused=1 turns on the LJ terms inside the traversal (QBVH_OPT_FUSED_LJ)
-    """Build, then one qbvh_query_lj_async call; returns rows, counts, status and the LJ outputs."""
+    """Build, then one qbvh_query_lj_async call; returns rows, counts, status and the LJ outputs.
+    fused=1 turns on the LJ terms inside the traversal (QBVH_OPT_FUSED_LJ)."""
     import torch
 
     from paper_1901_08088_gb300 import NeighborList, _lib
