@@ -107,12 +107,23 @@ class ClockSampler:
 # options of each entry and the traversal sources whose SHA-256 prefix is given; any
 # other source or options report null.
 PROFILED_TRAFFIC = {
-    "source_sha256": "601be1c201b2f701",
+    "source_sha256": "62af897e4941e35d",
     "entries": [
-        {"options": {"bundle_k": 64, "node_format": 0, "traversal": 1, "warp_particles": 32, "query_block": 256},
-         "bytes": 103.08e6 + 990.69e6, "warp_inst": 1711776670},
-        {"options": {"bundle_k": 64, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256},
-         "bytes": 102.99e6 + 992.95e6, "warp_inst": 1630920430},
+        {"options": {"bundle_k": 64, "node_format": 0, "traversal": 1, "warp_particles": 32, "query_block": 128,
+                     "fused_lj": 0},
+         "bytes": 104.72e6 + 1003.59e6, "warp_inst": 1398284582},
+        {"options": {"bundle_k": 64, "node_format": 0, "traversal": 1, "warp_particles": 32, "query_block": 256,
+                     "fused_lj": 0},
+         "bytes": 104.62e6 + 1002.97e6, "warp_inst": 1398284582},
+        {"options": {"bundle_k": 64, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 128,
+                     "fused_lj": 0},
+         "bytes": 102.95e6 + 986.15e6, "warp_inst": 1376329116},
+        {"options": {"bundle_k": 64, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256,
+                     "fused_lj": 0},
+         "bytes": 103.17e6 + 986.12e6, "warp_inst": 1376329132},
+        {"options": {"bundle_k": 64, "node_format": 0, "traversal": 1, "warp_particles": 32, "query_block": 128,
+                     "fused_lj": 1},
+         "bytes": 102.46e6 + 1014.56e6, "warp_inst": 1987695076},
     ],
 }
 # kernels of one timed step: build = prepare, Morton (+ sort histograms), segment
