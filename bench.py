@@ -255,6 +255,8 @@ def run_ours(args):
         explicit[_lib.QBVH_OPT_LJ_ZORDER] = args.lj_zorder
     if args.fused_lj >= 0:
         explicit[_lib.QBVH_OPT_FUSED_LJ] = args.fused_lj
+    if args.persistent >= 0:
+        explicit[_lib.QBVH_OPT_PERSISTENT] = args.persistent
     tuned, tune_evals = dict(explicit), 0
     if not args.no_autotune:
         def tune_step(opts):
@@ -570,7 +572,7 @@ def run_batched(args, local):
         g.replay()
 
     space = {k: autotune.OPTION_SPACE[k] for k in (_lib.QBVH_OPT_BUNDLE, _lib.QBVH_OPT_NODE_FORMAT,
-                                                   _lib.QBVH_OPT_QUERY_BLOCK)}
+                                                   _lib.QBVH_OPT_QUERY_BLOCK, _lib.QBVH_OPT_PERSISTENT)}
     best, _, _ = autotune.tune(graph_step, space=space, reps=3, warmup=1, sweeps=1)
     g = runners[tuple(sorted(best.items()))]
     for x in runners.values():
@@ -1032,6 +1034,8 @@ def main():
     ap.add_argument("--warp-particles", type=int, default=0, help="particles per warp of the walk (0: default)")
     ap.add_argument("--node-format", type=int, default=-1,
                     help="0: 10-bit quantized nodes, 1: FP32 nodes (-1: library default)")
+    ap.add_argument("--persistent", type=int, default=-1,
+                    help="traversal warps take packets from a queue (1) or one packet per warp (0); -1: autotuned")
     ap.add_argument("--fused-lj", type=int, default=-1,
                     help="LJ terms inside the traversal (1) or a separate list pass (0); -1: autotuned")
     ap.add_argument("--traversal", type=int, default=-1,

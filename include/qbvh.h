@@ -154,6 +154,13 @@ int qbvh_destroy(qbvh_handle h);
  * the two passes are faster; the autotuner decides per workload.  Takes
  * effect at the next call. */
 #define QBVH_OPT_FUSED_LJ 12
+/* Traversal work distribution for the one-particle-per-lane walk of exact
+ * FP32 lists: 0 (default) = one warp of the grid per packet of 32 Z-order
+ * particles; 1 = about as many warps as the GPU keeps resident, each taking
+ * packets from a device-side queue until none are left (a warp that ends
+ * early starts another packet instead of waiting for its block).  The list
+ * is the same either way.  Takes effect at the next query. */
+#define QBVH_OPT_PERSISTENT 13
 
 int qbvh_set_option(qbvh_handle h, int option, int value);
 int qbvh_get_option(qbvh_handle h, int option, int *value);
@@ -234,7 +241,7 @@ int qbvh_build_batched(qbvh_handle h, const void *pos_dev, int n_total, int n_sy
  * max_retries : when some row has more than cap neighbors the capacity is
  *               raised to the largest count rounded up to 32 and the traversal
  *               rerun (tree reused), at most max_retries times.
- * Blocks the host on one 8-byte readback per traversal (the largest count and
+ * Blocks the host on one 16-byte readback per traversal (the largest count and
  * the device error word).
  * Errors: NOT_BUILT, INVALID_ARG, CUTOFF_TOO_LARGE, OUT_OF_BOX, BAD_TYPE,
  *         OVERFLOW (counts complete, rows truncated), DEVICE_TIMEOUT, OOM, CUDA.
@@ -244,7 +251,7 @@ int qbvh_query(qbvh_handle h, const float *r_list_host, int cap, int max_retries
 
 /*
  * Enqueue one traversal without waiting: the list is written with capacity
- * cap and the 8-byte status is copied to the handle's pinned host memory on
+ * cap and the 16-byte status is copied to the handle's pinned host memory on
  * `stream`.  No host synchronization, no allocation once the row buffer
  * holds n*cap entries, so the call may be recorded into a CUDA graph after a
  * first call at the same sizes.  Read the outcome with qbvh_query_status once

@@ -37,6 +37,7 @@ QBVH_OPT_GRID_LANES = 9
 QBVH_OPT_WARP_PARTICLES = 10
 QBVH_OPT_TYPE_TREES = 11
 QBVH_OPT_FUSED_LJ = 12
+QBVH_OPT_PERSISTENT = 13
 
 _lock = threading.Lock()
 _lib = None

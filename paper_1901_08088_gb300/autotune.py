@@ -4,8 +4,9 @@ The paper lets runtime autotuners pick the kernel launch parameters during
 warm-up and then freezes them (Sec. 4).  Here the tuned options are the
 subtree-collapse size, the node format (10-bit or 21-bit quantized, or FP32
 bounds: the bit width of the quantization, Sec. 2.2), the
-traversal mapping (thread or warp per particle), the traversal block size and
-the lanes per particle of the LJ pass; where every type pair has the same
+traversal mapping (thread or warp per particle), the traversal block size,
+whether traversal warps take packets from a queue, and the lanes per particle
+of the LJ pass; where every type pair has the same
 list radius a caller may add one tree per system instead of one per type.
 The search is coordinate descent:
 each option in turn is swept with the others held at the best values so far,
@@ -30,6 +31,7 @@ OPTION_SPACE = {
     _lib.QBVH_OPT_WARP_PARTICLES: [32, 16, 8, 4, 1],
     _lib.QBVH_OPT_QUERY_BLOCK: [64, 128, 256],
     _lib.QBVH_OPT_LJ_LANES: [1, 2, 4, 8],
+    _lib.QBVH_OPT_PERSISTENT: [0, 1],
 }
 
 # options a caller adds to the search where they apply: one tree per system
@@ -49,6 +51,7 @@ DEFAULTS = {
     _lib.QBVH_OPT_LJ_LANES: 2,
     _lib.QBVH_OPT_TYPE_TREES: 1,
     _lib.QBVH_OPT_FUSED_LJ: 0,
+    _lib.QBVH_OPT_PERSISTENT: 0,
 }
 
 _NAMES = {
@@ -63,6 +66,7 @@ _NAMES = {
     _lib.QBVH_OPT_LJ_ZORDER: "lj_zorder",
     _lib.QBVH_OPT_TYPE_TREES: "type_trees",
     _lib.QBVH_OPT_FUSED_LJ: "fused_lj",
+    _lib.QBVH_OPT_PERSISTENT: "persistent",
 }
 
 

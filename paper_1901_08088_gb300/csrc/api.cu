@@ -73,6 +73,7 @@ struct qbvh_ctx {
     int grid_tpp = 8;      // lanes per particle of the grid traversal
     int type_trees = 1;    // 1: one tree per (system, type); 0: one tree per system
     int fused_lj = 0;      // qbvh_query_lj_async: LJ terms inside the traversal where supported
+    int persistent = 0;    // traversal warps take packets from a queue
     int built_method = 0;
     const void *grid_pos = nullptr;   // positions recorded by a grid-method build
     int built_fmt = 0;     // node format of the last build
@@ -493,7 +494,9 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
     rc = rc ? rc : ensure(h, h->counts, (size_t)(h->n > 0 ? h->n : 1) * 4);
     if (rc) return rc;
     DevStatus *st = reinterpret_cast<DevStatus *>(h->status.p);
-    if (cudaMemsetAsync(&st->max_count, 0, sizeof(int), s) != cudaSuccess) return QBVH_ERR_CUDA;
+    // the largest count and the traversal's packet queue start at zero (the
+    // error word keeps what the build found)
+    if (cudaMemsetAsync(&st->max_count, 0, 2 * sizeof(int), s) != cudaSuccess) return QBVH_ERR_CUDA;
     if (h->built_method == 1) {
         rc = grid_enqueue(h, q.r_list, q.rl2, cap, s);
         if (rc) return rc;
@@ -526,6 +529,7 @@ int query_enqueue(qbvh_ctx *h, const float *r_list_host, int cap, cudaStream_t s
     q.traversal = h->traversal;
     q.warp_particles = h->warp_particles;
     q.block = h->query_block;
+    q.persistent = h->persistent;
     q.f64 = h->f64 ? 1 : 0;
     q.leaves64 = h->f64 ? reinterpret_cast<const double4_32a *>(h->leaves64.p) : nullptr;
     q.L64 = h->L64;
@@ -683,6 +687,10 @@ int qbvh_set_option(qbvh_handle h, int option, int value)
         if (value != 0 && value != 1) return QBVH_ERR_INVALID_ARG;
         h->fused_lj = value;
         return QBVH_OK;
+    case QBVH_OPT_PERSISTENT:
+        if (value != 0 && value != 1) return QBVH_ERR_INVALID_ARG;
+        h->persistent = value;
+        return QBVH_OK;
     default: return QBVH_ERR_INVALID_ARG;
     }
 }
@@ -703,6 +711,7 @@ int qbvh_get_option(qbvh_handle h, int option, int *value)
     case QBVH_OPT_GRID_LANES: *value = h->grid_tpp; return QBVH_OK;
     case QBVH_OPT_TYPE_TREES: *value = h->type_trees; return QBVH_OK;
     case QBVH_OPT_FUSED_LJ: *value = h->fused_lj; return QBVH_OK;
+    case QBVH_OPT_PERSISTENT: *value = h->persistent; return QBVH_OK;
     default: return QBVH_ERR_INVALID_ARG;
     }
 }

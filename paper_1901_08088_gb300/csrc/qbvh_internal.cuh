@@ -320,7 +320,9 @@ struct SysInfo {
 
 struct DevStatus {
     int max_count;
+    unsigned next_packet;   // packet queue of the traversal (zeroed with max_count before each query)
     unsigned err;
+    unsigned pad;
 };
 
 // ---- launchers (build.cu) ------------------------------------------------
@@ -418,6 +420,8 @@ struct QueryArgs {
     float rl2_hi[64];
     double r2_64[64];
     int block;
+    int persistent;        // 1: resident warps take packets from a queue (one particle per lane)
+    int n_packets;         // packets of 32 / W particles
     int sparse_blocks;     // leading blocks that walk sparse trees one particle per warp
     float r_list[64];      // [a][b] list radius
     float rl2[64];         // fl(r * r)

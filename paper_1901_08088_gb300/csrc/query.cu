@@ -1432,8 +1432,10 @@ __device__ __forceinline__ void lj_block_record(const QueryArgs &a, double v0, d
     }
 }
 
+// One packet: the G = 32 / W consecutive Z-order particles p G, ..., p G + G - 1
+// walked by this warp.  Every lane of the warp calls this together.
 template <bool WIDE, bool CAND, int FMT, int W, bool ONE, int PHASE, bool F64, bool LJ>
-__device__ __forceinline__ void warp_query(const QueryArgs &a)
+__device__ __forceinline__ void warp_packet(const QueryArgs &a, int p)
 {
     static_assert(!LJ || (ONE && W == 1 && !CAND && !F64 && PHASE == 2), "LJ terms: one tree, filtered walk");
     constexpr int G = 32 / W;
@@ -1443,23 +1445,7 @@ __device__ __forceinline__ void warp_query(const QueryArgs &a)
     const int pidx = lane % G;
     const int wsub = lane / G;
     const unsigned same = same_lanes(W) << pidx;
-    int bid = (int)blockIdx.x, nblk = (int)gridDim.x;
-    if (SPARSE && a.sparse_blocks > 0) {
-        if (bid < a.sparse_blocks) {
-            sparse_walks<FMT>(a);
-            return;
-        }
-        bid -= a.sparse_blocks;
-        nblk -= a.sparse_blocks;
-    }
-    // with several types, blocks take the sorted order from its end: the last
-    // trees (in a size-asymmetric mixture the large particles, whose packets
-    // span wide regions and walk longest) start first and overlap the rest
-    // instead of running alone at the end (mixture L = 100: 2.05 -> 1.89 ms
-    // before sparse trees; one type gains nothing from it, 1.84 -> 1.87 ms at
-    // N = 2M)
-    const int blk = (QBVH_REVERSE_BLOCKS && (ONE ? 1 : a.n_types) > 1) ? nblk - 1 - bid : bid;
-    const int s = ((blk * blockDim.x + threadIdx.x) >> 5) * G + pidx;
+    const int s = p * G + pidx;
     const bool active = s < a.n;
     float4 me = make_float4(0.f, 0.f, 0.f, 0.f);
     int i_orig = 0, seg_i = -1;
@@ -1593,17 +1579,65 @@ __device__ __forceinline__ void warp_query(const QueryArgs &a)
     }
 }
 
+// Packets to warps.  Without PERSIST every warp of the grid walks one packet
+// (its index in the grid).  With PERSIST the grid holds about as many warps
+// as the GPU keeps resident, and each warp takes packets from a device
+// counter until they run out, so that a warp that ends early starts the next
+// packet instead of idling until its block's last warp ends.  The counter
+// only grows, so the loop ends.  With several types packets are taken from
+// the end of the sorted order first: the last trees (in a size-asymmetric
+// mixture the large particles, whose packets span wide regions and walk
+// longest) start first and overlap the rest instead of running alone at the
+// end (mixture L = 100: 2.05 -> 1.89 ms before sparse trees; one type gains
+// nothing from it, 1.84 -> 1.87 ms at N = 2M).
+template <bool WIDE, bool CAND, int FMT, int W, bool ONE, int PHASE, bool F64, bool LJ, bool PERSIST>
+__device__ __forceinline__ void warp_query(const QueryArgs &a)
+{
+    static_assert(!PERSIST || (!LJ && PHASE == 2), "packet queue: one launch, no per-block LJ records");
+    constexpr bool SPARSE = QBVH_SPARSE_TREES && !WIDE && !ONE && !CAND && !F64 && PHASE == 2;
+    int bid = (int)blockIdx.x, nblk = (int)gridDim.x;
+    if (SPARSE && a.sparse_blocks > 0) {
+        if (bid < a.sparse_blocks) {
+            sparse_walks<FMT>(a);
+            return;
+        }
+        bid -= a.sparse_blocks;
+        nblk -= a.sparse_blocks;
+    }
+    const bool rev = QBVH_REVERSE_BLOCKS && (ONE ? 1 : a.n_types) > 1;
+    if (PERSIST) {
+        const int lane = threadIdx.x & 31;
+        for (;;) {
+            int p = 0;
+            if (lane == 0) p = (int)atomicAdd(&a.status->next_packet, 1u);
+            p = __shfl_sync(FULL, p, 0);
+            if (p >= a.n_packets) break;
+            warp_packet<WIDE, CAND, FMT, W, ONE, PHASE, F64, LJ>(a, rev ? a.n_packets - 1 - p : p);
+        }
+        return;
+    }
+    const int blk = rev ? nblk - 1 - bid : bid;
+    warp_packet<WIDE, CAND, FMT, W, ONE, PHASE, F64, LJ>(a, (int)((blk * blockDim.x + threadIdx.x) >> 5));
+}
+
 template <bool WIDE, bool CAND, int FMT, int W, bool ONE, int PHASE, bool F64 = false>
 __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ QueryArgs a)
 {
-    warp_query<WIDE, CAND, FMT, W, ONE, PHASE, F64, false>(a);
+    warp_query<WIDE, CAND, FMT, W, ONE, PHASE, F64, false, false>(a);
+}
+
+// the one-particle-per-lane walk of exact FP32 lists with the packet queue
+template <bool WIDE, int FMT, bool ONE>
+__global__ void QBVH_QUERY_BOUNDS query_queue_kernel(const __grid_constant__ QueryArgs a)
+{
+    warp_query<WIDE, false, FMT, 1, ONE, 2, false, false, true>(a);
 }
 
 // the walk of one system of one type that also sums the LJ terms of its pairs
 template <int FMT>
 __global__ void __launch_bounds__(256, QBVH_QUERY_LJ_MIN_BLOCKS) query_warp_lj_kernel(const __grid_constant__ QueryArgs a)
 {
-    warp_query<false, false, FMT, 1, true, 2, false, true>(a);
+    warp_query<false, false, FMT, 1, true, 2, false, true, false>(a);
 }
 
 }  // namespace
@@ -1643,16 +1677,46 @@ static size_t stage_bytes(int block, bool stage)
     return stage ? (size_t)(block / 32) * sizeof(BundleStage) : 0;
 }
 
+// Blocks of `kernel` that one SM keeps resident at `block` threads and
+// `smem` bytes of dynamic shared memory (at least 1).
+static int resident_blocks(const void *kernel, int block, size_t smem)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, smem) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    return nb;
+}
+
+// The packet-queue walk: at most as many blocks as stay resident, plus the
+// sparse-tree blocks.
+template <int FMT, bool WIDE, bool ONE>
+static void launch_queue(QueryArgs a, cudaStream_t s, int grid, size_t sm)
+{
+    const void *k = reinterpret_cast<const void *>(&query_queue_kernel<WIDE, FMT, ONE>);
+    const int resident = sm_count_current() * resident_blocks(k, a.block, sm);
+    const int g = min(grid, resident) + a.sparse_blocks;
+    query_queue_kernel<WIDE, FMT, ONE><<<g, a.block, sm, s>>>(a);
+}
+
 template <int FMT, int W, int PHASE>
 static void launch_warp_phase(QueryArgs a, cudaStream_t s, int grid)
 {
     const int b = a.block;
     a.sparse_blocks = 0;
+    a.n_packets = grid * (b / 32);
     if (QBVH_SPARSE_TREES && PHASE == 2 && !a.wide_keys && !a.candidates && a.n_types > 1) {
         a.sparse_blocks = sparse_blocks_for(a);
         grid += a.sparse_blocks;
     }
     const size_t sm = stage_bytes(b, stage_on(W, a.candidates != 0, false));
+    if (PHASE == 2 && W == 1 && a.persistent && !a.candidates) {
+        if (a.wide_keys) launch_queue<FMT, true, false>(a, s, grid - a.sparse_blocks, sm);
+        else if (a.n_types == 1) launch_queue<FMT, false, true>(a, s, grid - a.sparse_blocks, sm);
+        else launch_queue<FMT, false, false>(a, s, grid - a.sparse_blocks, sm);
+        return;
+    }
     if (a.wide_keys) {
         if (a.candidates) query_warp_kernel<true, true, FMT, W, false, PHASE><<<grid, b, sm, s>>>(a);
         else query_warp_kernel<true, false, FMT, W, false, PHASE><<<grid, b, sm, s>>>(a);

@@ -36,7 +36,7 @@ def assert_same_lists(rows_g, counts_g, rows_o, counts_o, idx=None):
 
 
 def gpu_list(system, cap=256, bundle=None, block=None, candidates=None, max_retries=4, traversal=None,
-             node_format=None, method=None, grid_lanes=None, warp_particles=None):
+             node_format=None, method=None, grid_lanes=None, warp_particles=None, persistent=None):
     import torch
     from paper_1901_08088_gb300 import NeighborList, _lib
 
@@ -57,6 +57,8 @@ def gpu_list(system, cap=256, bundle=None, block=None, candidates=None, max_retr
         nl.set_option(_lib.QBVH_OPT_WARP_PARTICLES, warp_particles)
     if grid_lanes is not None:
         nl.set_option(_lib.QBVH_OPT_GRID_LANES, grid_lanes)
+    if persistent is not None:
+        nl.set_option(_lib.QBVH_OPT_PERSISTENT, persistent)
     pos4 = torch.from_numpy(workloads.pack_float4(system.pos, system.types)).cuda()
     nl.build(pos4, system.L, system.n_types)
     nl.query(system.r_list, cap=cap, max_retries=max_retries)
