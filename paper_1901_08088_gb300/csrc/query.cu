@@ -853,10 +853,13 @@ __host__ __device__ constexpr bool stage_on(int W, bool CAND, bool F64)
     return QBVH_PREFILTER && W == 1 && !CAND && !F64;
 }
 
+// A bundle's survivors (at most 64, padded to an even count) are staged
+// before they are tested, so that every bundle runs one survivor loop.
+constexpr int kStage = 64;
 struct BundleStage {
     float4 blo, bhi;      // the warp's box of image centres (x, y, z)
-    float x[32], y[32], z[32];
-    int id[32];           // original indices of the survivors
+    float x[kStage], y[kStage], z[kStage];   // 16-byte aligned: four survivors per load
+    int id[kStage];       // original indices of the survivors
     union {
         int owner[32];    // overlapping lanes, in lane order (spread, without staging)
         int ring[16 * 32];   // row staging: slot k of lane l at ring[32 k + l]
@@ -965,14 +968,12 @@ struct LJCtx {
     float sig2, rc2;
 };
 
+// Two survivors (x, y, z as packed pairs, original indices id) against the
+// lane's particle.
 template <bool SHIFT, bool SELF, bool LJ = false>
-__device__ __forceinline__ void survivor_pair(const Query &c, Row &out, int t, bool on, const BundleStage *st,
-                                              bool staged, const LJCtx &lj = LJCtx{})
+__device__ __forceinline__ void survivor_vals(const Query &c, Row &out, const f32x2 X, const f32x2 Y, const f32x2 Z,
+                                              const int2 id, bool on, bool staged, const LJCtx &lj)
 {
-    const f32x2 X = *reinterpret_cast<const f32x2 *>(st->x + t);
-    const f32x2 Y = *reinterpret_cast<const f32x2 *>(st->y + t);
-    const f32x2 Z = *reinterpret_cast<const f32x2 *>(st->z + t);
-    const int2 id = *reinterpret_cast<const int2 *>(st->id + t);
     f32x2 dx = f2_sub(X, f2_pack(c.xi, c.xi)), dy = f2_sub(Y, f2_pack(c.yi, c.yi)),
           dz = f2_sub(Z, f2_pack(c.zi, c.zi));
     if (SHIFT) {
@@ -1013,6 +1014,33 @@ __device__ __forceinline__ void survivor_pair(const Query &c, Row &out, int t, b
     }
 }
 
+// survivors t, t + 1 of the stage (8-byte loads)
+template <bool SHIFT, bool SELF, bool LJ = false>
+__device__ __forceinline__ void survivor_pair(const Query &c, Row &out, int t, bool on, const BundleStage *st,
+                                              bool staged, const LJCtx &lj = LJCtx{})
+{
+    survivor_vals<SHIFT, SELF, LJ>(c, out, *reinterpret_cast<const f32x2 *>(st->x + t),
+                                   *reinterpret_cast<const f32x2 *>(st->y + t),
+                                   *reinterpret_cast<const f32x2 *>(st->z + t),
+                                   *reinterpret_cast<const int2 *>(st->id + t), on, staged, lj);
+}
+
+// survivors t .. t + 3 of the stage, t a multiple of 4 (16-byte loads; each
+// half of a loaded float4 is an aligned register pair)
+template <bool SHIFT, bool SELF, bool LJ = false>
+__device__ __forceinline__ void survivor_quad(const Query &c, Row &out, int t, bool on, const BundleStage *st,
+                                              const LJCtx &lj)
+{
+    const float4 X = *reinterpret_cast<const float4 *>(st->x + t);
+    const float4 Y = *reinterpret_cast<const float4 *>(st->y + t);
+    const float4 Z = *reinterpret_cast<const float4 *>(st->z + t);
+    const int4 I = *reinterpret_cast<const int4 *>(st->id + t);
+    survivor_vals<SHIFT, SELF, LJ>(c, out, f2_pack(X.x, X.y), f2_pack(Y.x, Y.y), f2_pack(Z.x, Z.y),
+                                   make_int2(I.x, I.y), on, true, lj);
+    survivor_vals<SHIFT, SELF, LJ>(c, out, f2_pack(X.z, X.w), f2_pack(Y.z, Y.w), f2_pack(Z.z, Z.w),
+                                   make_int2(I.z, I.w), on, true, lj);
+}
+
 // Every lane tests every survivor (one particle per lane), two per step: the
 // differences and squares as packed f32x2 pairs, the two sums as scalar adds
 // -- the same operations in the same order as exact_d2.  (ptxas contracts a
@@ -1029,10 +1057,8 @@ __device__ __forceinline__ void survivors_loop(const Query &c, Row &out, int s, 
     int t = 0;
     if (staged) {
         for (; t + 8 <= s; t += 8) {
-            survivor_pair<SHIFT, SELF, LJ>(c, out, t, on, st, true, lj);
-            survivor_pair<SHIFT, SELF, LJ>(c, out, t + 2, on, st, true, lj);
-            survivor_pair<SHIFT, SELF, LJ>(c, out, t + 4, on, st, true, lj);
-            survivor_pair<SHIFT, SELF, LJ>(c, out, t + 6, on, st, true, lj);
+            survivor_quad<SHIFT, SELF, LJ>(c, out, t, on, st, lj);
+            survivor_quad<SHIFT, SELF, LJ>(c, out, t + 4, on, st, lj);
             out.check();
         }
     }
@@ -1135,14 +1161,67 @@ __device__ __forceinline__ void bundle_chunk(const QueryArgs &a, const Query &c,
     __syncwarp();   // the next bundle rewrites the stage
 }
 
-// A bundle of cnt <= 64 leaves, in chunks of 32 (one leaf per lane).
+// The filter of a chunk of cnt <= 32 leaves starting at `first`: its
+// survivors are appended to the stage after the s already there; returns the
+// new count (warp-uniform).  Every lane of the warp calls this together.
+__device__ __forceinline__ int chunk_filter(const QueryArgs &a, int first, int cnt, float rs2, BundleStage *st,
+                                            int s)
+{
+    const int lane = threadIdx.x & 31;
+    const bool v = lane < cnt;
+    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (v) q = tree_ld(a.leaves + first + lane);
+    const float4 lo = st->blo, hi = st->bhi;
+    const float gx = fmaxf(fmaxf(__fsub_rd(lo.x, q.x), __fsub_rd(q.x, hi.x)), 0.f);
+    const float gy = fmaxf(fmaxf(__fsub_rd(lo.y, q.y), __fsub_rd(q.y, hi.y)), 0.f);
+    const float gz = fmaxf(fmaxf(__fsub_rd(lo.z, q.z), __fsub_rd(q.z, hi.z)), 0.f);
+    const float g2 = __fmaf_rd(gx, gx, __fmaf_rd(gy, gy, __fmul_rd(gz, gz)));
+    const bool surv = v && g2 <= rs2;
+    const unsigned S = __ballot_sync(FULL, surv);
+    if (surv) {
+        unsigned lt;
+        asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+        const int r = s + __popc(S & lt);
+        st->x[r] = q.x;
+        st->y[r] = q.y;
+        st->z[r] = q.z;
+        st->id[r] = __float_as_int(q.w) & 0x7FFFFFFF;
+    }
+    return s + __popc(S);
+}
+
+// A bundle of cnt <= 64 leaves.  Both 32-leaf chunks are filtered into the
+// stage first and the survivors tested in one loop.  An odd count is padded
+// with a point at 1e30 in every coordinate: its squared distance overflows to
+// +inf, so no lane accepts it, and its LJ terms are zero.  (With the spread
+// of few-lane bundles, a build option without row staging, chunks are tested
+// one at a time.)
 template <bool SHIFT, bool SELF, bool LJ = false>
 __device__ __forceinline__ void bundle_filtered(const QueryArgs &a, const Query &c, Row &out, int first, int cnt,
                                                 unsigned hm, bool on, float rs2, BundleStage *st,
                                                 const LJCtx &lj = LJCtx{})
 {
-    for (int base = 0; base < cnt; base += 32)
-        bundle_chunk<SHIFT, SELF, LJ>(a, c, out, first + base, min(32, cnt - base), hm, on, rs2, st, lj);
+    constexpr bool PER_CHUNK = QBVH_FILTER_SPREAD && !QBVH_ROW_STAGING;
+    if (PER_CHUNK) {
+        for (int base = 0; base < cnt; base += 32)
+            bundle_chunk<SHIFT, SELF, LJ>(a, c, out, first + base, min(32, cnt - base), hm, on, rs2, st, lj);
+        return;
+    }
+    int s = 0;
+    for (int base = 0; base < cnt; base += 32) s = chunk_filter(a, first + base, min(32, cnt - base), rs2, st, s);
+    if (s == 0) return;
+    if (s & 1) {
+        if ((threadIdx.x & 31) == 0) {
+            st->x[s] = 1e30f;
+            st->y[s] = 1e30f;
+            st->z[s] = 1e30f;
+            st->id[s] = 0;
+        }
+        ++s;
+    }
+    __syncwarp();
+    survivors_loop<SHIFT, SELF, LJ>(c, out, s, on, st, lj);
+    __syncwarp();   // the next bundle rewrites the stage
 }
 
 // bundle leaves tested two per step (two loads in flight; measured 2.25 ->
