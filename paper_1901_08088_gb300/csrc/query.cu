@@ -129,13 +129,15 @@ __device__ __forceinline__ Node decode_21(const float4 a, const float4 b, const 
 }
 
 // Read-only loads of tree words (nodes, leaves).  QBVH_TREE_EVICT_LAST = 1
-// marks them evict-last in L2, so that the list writes streaming through L2
-// (about 1.4 GB of DRAM writes per launch at N = 2M, against a 96 MB tree)
-// evict them after everything else: query 1.92 -> 1.84 ms at N = 2M.
+// marks them evict-last in L2, so that list writes streaming through L2 evict
+// them after everything else.  That paid while the list went out as 4-byte
+// stores (1.4 GB of DRAM writes per launch at N = 2M: query 1.92 -> 1.84 ms);
+// with whole-sector row writes (1.0 GB) plain loads are faster (10-bit nodes
+// 1.266 -> 1.240 ms, FP32 nodes 1.243 -> 1.237 ms), so it is off.
 // QBVH_NODE_V8 = 1 reads a 32-byte FP32 node with one 256-bit load (sm_100
 // and later) instead of two 128-bit ones (same speed, one instruction).
 #ifndef QBVH_TREE_EVICT_LAST
-#define QBVH_TREE_EVICT_LAST 1
+#define QBVH_TREE_EVICT_LAST 0
 #endif
 #ifndef QBVH_NODE_V8
 #define QBVH_NODE_V8 1
