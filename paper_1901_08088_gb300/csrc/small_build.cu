@@ -17,11 +17,6 @@ namespace qbvh {
 
 namespace {
 
-// sort of the keys: a bitonic network over unique 64-bit keys (1) or a
-// stable LSD radix sort with 8-bit digits (0)
-#ifndef QBVH_SMALL_BITONIC
-#define QBVH_SMALL_BITONIC 1
-#endif
 constexpr int kSB = 1024;                    // threads of the block
 constexpr int kSmallMax = 4096;              // largest system
 constexpr int kItems = kSmallMax / kSB;      // keys per thread
@@ -139,12 +134,8 @@ __global__ void __launch_bounds__(kSB, 1) small_build_kernel(const BuildArgs a)
                 acc[t][6] = max(acc[t][6], __float_as_uint(p.z));
             }
         }
-#if QBVH_SMALL_BITONIC
-        reinterpret_cast<unsigned long long *>(kA)[i] = ((unsigned long long)key << 32) | (unsigned)i;
-#else
         kA[i] = key;
         vA[i] = i;
-#endif
     }
 #pragma unroll
     for (int t = 0; t < kMaxTrees; ++t) {
@@ -205,42 +196,6 @@ __global__ void __launch_bounds__(kSB, 1) small_build_kernel(const BuildArgs a)
         if (tid == T - 1) a.seg_start[T] = start + c;
     }
 
-#if QBVH_SMALL_BITONIC
-    // ---- sort of the unique 64-bit keys (key << 32 | input index) ------------
-    // A bitonic network over the next power of two >= n (entries past n hold
-    // key 0xFFFFFFFF and an index >= n, so they sort last).  The keys are
-    // unique, so the order is the stable sort of the 32-bit keys with the
-    // input index as the value: the order of the multi-kernel build.
-    {
-        unsigned long long *K64 = reinterpret_cast<unsigned long long *>(kA);   // kA and vA together
-        int P = 2;
-        while (P < n) P <<= 1;
-        __syncthreads();
-        for (int k = 2; k <= P; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int t = tid; t < P / 2; t += kSB) {
-                    const int i = 2 * t - (t & (j - 1));   // bit j of i is clear
-                    const unsigned long long x = K64[i], y = K64[i + j];
-                    if ((x > y) == ((i & k) == 0)) {
-                        K64[i] = y;
-                        K64[i + j] = x;
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        unsigned long long kv[kItems];
-#pragma unroll
-        for (int it = 0; it < kItems; ++it) kv[it] = K64[tid + it * kSB];
-        __syncthreads();
-#pragma unroll
-        for (int it = 0; it < kItems; ++it) {
-            kA[tid + it * kSB] = (unsigned)(kv[it] >> 32);
-            vA[tid + it * kSB] = (int)(unsigned)kv[it];
-        }
-        __syncthreads();
-    }
-#else
     // ---- stable LSD radix sort of (key, input index), 8-bit digits ---------
     // (each warp ranks its run row by row, lanes in order; runs keep the warp
     // order, so equal digits keep their order: the sort is stable, and with
@@ -309,8 +264,7 @@ __global__ void __launch_bounds__(kSB, 1) small_build_kernel(const BuildArgs a)
         src_v = dst_v;
         dst_v = tv;
     }
-#endif
-    // the sorted keys and their input indices are in kA / vA
+    // four passes: the result is back in kA / vA
     unsigned *out_keys = const_cast<unsigned *>(reinterpret_cast<const unsigned *>(a.keys_sorted));
     int *out_order = const_cast<int *>(a.order);
     for (int k = tid; k < n; k += kSB) {
@@ -459,6 +413,10 @@ __global__ void __launch_bounds__(kSB, 1) small_build_kernel(const BuildArgs a)
 // N = 1000 0.091 / 0.076 vs 0.134 / 0.108, N = 3000 0.127 / 0.114 vs 0.155 /
 // 0.130, N = 4096 0.142 / 0.132 vs 0.142 / 0.117.  At 4096 one SM's sort
 // (51k cycles), hierarchy (32k) and fit (27k) no longer beat 152 SMs.
+// (Measured again later, build alone at N = 4096: 0.083 ms eager against
+// 0.088 ms for the nine-launch build, which replays faster from a graph; a
+// bitonic sort of unique 64-bit keys instead of the radix sort measured
+// slower: 0.082 against 0.067 ms at N = 3072.)
 #ifndef QBVH_SMALL_USE
 #define QBVH_SMALL_USE 3072
 #endif
