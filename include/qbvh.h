@@ -127,8 +127,11 @@ int qbvh_destroy(qbvh_handle h);
  * n * value must stay below 2^32 (else qbvh_query: QBVH_ERR_INVALID_ARG). */
 #define QBVH_OPT_GRID_LANES 9
 /* Particles per warp of the warp-uniform walk: 32 (default), 16, 8, 4, 2 or
- * 1; with fewer particles each particle gets 32/value lanes, which split a bundle's
- * leaves and pack their accepted neighbours with a ballot.  Fewer particles
+ * 1; with fewer particles each particle gets 32/value lanes.  With 2 or 4 lanes
+ * per particle (16 or 8 per warp) the lanes split the survivors of each
+ * bundle's filter and share the particle's row through their staging rings;
+ * with more lanes they split a bundle's leaves and pack their accepted
+ * neighbours with a ballot.  Fewer particles
  * per warp means more warps (small systems fill the GPU) and a smaller union
  * of search spheres per walk.  In a single-system build of 2 to 4 types,
  * a type of at most 4096 particles so sparse that 32 of them span more than

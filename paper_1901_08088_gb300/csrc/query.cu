@@ -292,6 +292,10 @@ __device__ __forceinline__ void row_store(int *p, int v)
 #ifndef QBVH_ROW_STAGING
 #define QBVH_ROW_STAGING 1
 #endif
+// zero image and the other images in two launches (see query_warp_kernel)
+#ifndef QBVH_QUERY_SPLIT_IMAGES
+#define QBVH_QUERY_SPLIT_IMAGES 0
+#endif
 __device__ __forceinline__ void store_sector(int *dst, const int *ring)
 {
     const int4 lo = make_int4(ring[0], ring[32], ring[64], ring[96]);
@@ -306,6 +310,7 @@ struct Row {
     int count;
     int *ring;   // this lane's slot 0 in the warp's staging ring, or nullptr
     int base;    // staging: entries [0, base) have left the ring (a multiple of 8)
+    int fill;    // staging with W lanes per particle: entries the group has written to the row
 
     // the completed sector [base, base + 8) (staging only)
     __device__ __forceinline__ void flush()
@@ -348,6 +353,49 @@ struct Row {
         check();
         const int end = min(count, cap);
         for (int k = base; k < end; ++k) row_store(row + k, ring[32 * (k & 15)]);
+    }
+
+    // With W > 1 lanes per particle (the lanes in `same`) every lane stages
+    // the survivors it tests in its own ring and counts its own accepted
+    // entries; the group shares the row.  A completed sector goes to the next
+    // free 8 slots of the row, in lane order among the lanes that flush
+    // together.  Every lane of the warp calls this together.
+    __device__ __forceinline__ void check_group(unsigned same)
+    {
+        const bool f = count - base >= 8;
+        const unsigned b = __ballot_sync(0xFFFFFFFFu, f) & same;
+        if (f) {
+            unsigned lt;
+            asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+            const int off = fill + 8 * __popc(b & lt);
+            if (off + 8 <= cap) store_sector(row + off, ring + 32 * (base & 15));
+            base += 8;
+        }
+        fill += 8 * __popc(b);
+    }
+
+    // The group's partial sectors after its complete ones, in lane order; then
+    // count holds the particle's total.  Every lane of the warp calls this
+    // together; `first` is the group's first lane, G the lane stride.
+    template <int W>
+    __device__ __forceinline__ void drain_group(unsigned same, int first, int G, int wsub)
+    {
+        check_group(same);
+        const int k = count - base;
+        int pre = 0, tot_left = 0, total = 0;
+#pragma unroll
+        for (int m = 0; m < W; ++m) {
+            const int km = __shfl_sync(0xFFFFFFFFu, k, first + m * G);
+            const int cm = __shfl_sync(0xFFFFFFFFu, count, first + m * G);
+            if (m < wsub) pre += km;
+            tot_left += km;
+            total += cm;
+        }
+        const int start = fill + pre;
+        for (int i = 0; i < k; ++i)
+            if (start + i < cap) row_store(row + start + i, ring[32 * ((base + i) & 15)]);
+        fill += tot_left;
+        count = total;
     }
 };
 
@@ -849,10 +897,17 @@ __device__ __forceinline__ bool cube_overlap(unsigned nlo, unsigned nhi, const L
 #ifndef QBVH_LOOP_COST
 #define QBVH_LOOP_COST 14
 #endif
-// the walks that filter bundles (one particle per lane, exact lists of FP32 data)
+// the walks that filter bundles: exact lists of FP32 data with one particle per
+// lane, or 2 or 4 lanes per particle (those share a row through the staging
+// ring, so they need it, and the one-launch walk)
+#ifndef QBVH_MULTI_LANE_FILTER
+#define QBVH_MULTI_LANE_FILTER 1
+#endif
 __host__ __device__ constexpr bool stage_on(int W, bool CAND, bool F64)
 {
-    return QBVH_PREFILTER && W == 1 && !CAND && !F64;
+    return QBVH_PREFILTER && !CAND && !F64 &&
+           (W == 1 || (QBVH_MULTI_LANE_FILTER && (W == 2 || W == 4) && QBVH_ROW_STAGING &&
+                       !QBVH_QUERY_SPLIT_IMAGES));
 }
 
 // A bundle's survivors (at most 64, padded to an even count) are staged
@@ -1077,6 +1132,31 @@ __device__ __forceinline__ void survivors_loop(const Query &c, Row &out, int s, 
     if (staged) out.check();
 }
 
+// W > 1 lanes per particle: lane wsub of a particle tests the survivor pairs
+// 2 (k W + wsub), k = 0, 1, ..., and stages what it accepts in its own ring
+// (s is a multiple of 2 W).  Between two checks a lane stages 8 survivors.
+template <bool SHIFT, bool SELF, int W>
+__device__ __forceinline__ void survivors_loop_w(const Query &c, Row &out, int s, bool on, const BundleStage *st,
+                                                 int wsub, unsigned same)
+{
+    const int steps = s / (2 * W);
+    int t = 2 * wsub;
+    int k = 0;
+    for (; k + 4 <= steps; k += 4) {
+        survivor_pair<SHIFT, SELF>(c, out, t, on, st, true);
+        survivor_pair<SHIFT, SELF>(c, out, t + 2 * W, on, st, true);
+        survivor_pair<SHIFT, SELF>(c, out, t + 4 * W, on, st, true);
+        survivor_pair<SHIFT, SELF>(c, out, t + 6 * W, on, st, true);
+        t += 8 * W;
+        out.check_group(same);
+    }
+    for (; k < steps; ++k) {
+        survivor_pair<SHIFT, SELF>(c, out, t, on, st, true);
+        t += 2 * W;
+    }
+    out.check_group(same);
+}
+
 // Survivors spread over the warp when few lanes overlap the bundle: the s
 // survivors occupy s lanes of each of kk = 32 / width slots (width 32, 16 or
 // 8 lanes), and each trip serves kk overlapping particles, whose centre,
@@ -1193,15 +1273,15 @@ __device__ __forceinline__ int chunk_filter(const QueryArgs &a, int first, int c
 }
 
 // A bundle of cnt <= 64 leaves.  Both 32-leaf chunks are filtered into the
-// stage first and the survivors tested in one loop.  An odd count is padded
-// with a point at 1e30 in every coordinate: its squared distance overflows to
-// +inf, so no lane accepts it, and its LJ terms are zero.  (With the spread
-// of few-lane bundles, a build option without row staging, chunks are tested
-// one at a time.)
-template <bool SHIFT, bool SELF, bool LJ = false>
+// stage first and the survivors tested in one loop.  The count is padded to a
+// multiple of 2 W with points at 1e30 in every coordinate: their squared
+// distance overflows to +inf, so no lane accepts them, and their LJ terms are
+// zero.  (With the spread of few-lane bundles, a build option without row
+// staging, chunks are tested one at a time.)
+template <bool SHIFT, bool SELF, bool LJ = false, int W = 1>
 __device__ __forceinline__ void bundle_filtered(const QueryArgs &a, const Query &c, Row &out, int first, int cnt,
                                                 unsigned hm, bool on, float rs2, BundleStage *st,
-                                                const LJCtx &lj = LJCtx{})
+                                                const LJCtx &lj = LJCtx{}, int wsub = 0, unsigned same = 0u)
 {
     constexpr bool PER_CHUNK = QBVH_FILTER_SPREAD && !QBVH_ROW_STAGING;
     if (PER_CHUNK) {
@@ -1212,17 +1292,18 @@ __device__ __forceinline__ void bundle_filtered(const QueryArgs &a, const Query 
     int s = 0;
     for (int base = 0; base < cnt; base += 32) s = chunk_filter(a, first + base, min(32, cnt - base), rs2, st, s);
     if (s == 0) return;
-    if (s & 1) {
-        if ((threadIdx.x & 31) == 0) {
-            st->x[s] = 1e30f;
-            st->y[s] = 1e30f;
-            st->z[s] = 1e30f;
-            st->id[s] = 0;
-        }
-        ++s;
+    const int pad = (2 * W - s % (2 * W)) % (2 * W);   // s <= 64, a multiple of 2 W: s + pad <= 64
+    const int lane = threadIdx.x & 31;
+    if (lane < pad) {
+        st->x[s + lane] = 1e30f;
+        st->y[s + lane] = 1e30f;
+        st->z[s + lane] = 1e30f;
+        st->id[s + lane] = 0;
     }
+    s += pad;
     __syncwarp();
-    survivors_loop<SHIFT, SELF, LJ>(c, out, s, on, st, lj);
+    if (W == 1) survivors_loop<SHIFT, SELF, LJ>(c, out, s, on, st, lj);
+    else survivors_loop_w<SHIFT, SELF, W>(c, out, s, on, st, wsub, same);
     __syncwarp();   // the next bundle rewrites the stage
 }
 
@@ -1309,8 +1390,12 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                     const bool self_here =
                         !SHIFT && __any_sync(FULL, (unsigned)(c.self - j) <= (unsigned)(l - j));
                     if (FILTER && l - j < 64) {
-                        if (self_here) bundle_filtered<SHIFT, true, LJ>(a, c, out, j, l - j + 1, hm, on, rs2, st, lj);
-                        else bundle_filtered<SHIFT, false, LJ>(a, c, out, j, l - j + 1, hm, on, rs2, st, lj);
+                        if (self_here)
+                            bundle_filtered<SHIFT, true, LJ, W>(a, c, out, j, l - j + 1, hm, on, rs2, st, lj, wsub,
+                                                                same);
+                        else
+                            bundle_filtered<SHIFT, false, LJ, W>(a, c, out, j, l - j + 1, hm, on, rs2, st, lj, wsub,
+                                                                 same);
                     } else if (W == 1 && !CAND && l - j < 32 && __popc(hm) <= QBVH_SPREAD_MAX) {
                         if (self_here) bundle_spread<SHIFT, F64, true>(a, c, out, j, l - j + 1, hm);
                         else bundle_spread<SHIFT, F64, false>(a, c, out, j, l - j + 1, hm);
@@ -1348,6 +1433,11 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                 if (acc) out.push(__float_as_int(q.w) & 0x7FFFFFFF);
             } else if (W == 1) {
                 if (on) test_leaf<CAND, SHIFT, F64, true, FMT>(a, c, out, j, q, f, rs2);
+            } else if (FILTER) {
+                // the group's row goes through the staging rings
+                const bool acc = wsub == 0 && on && leaf_accepts<CAND, SHIFT, F64, FMT>(a, c, j, q, f, rs2);
+                out.stage(__float_as_int(q.w) & 0x7FFFFFFF, acc);
+                out.check_group(same);
             } else {
                 const bool acc = wsub == 0 && on && leaf_accepts<CAND, SHIFT, F64, FMT>(a, c, j, q, f, rs2);
                 push_shared(out, acc, __float_as_int(q.w) & 0x7FFFFFFF, same);
@@ -1557,6 +1647,7 @@ __device__ __forceinline__ void warp_packet(const QueryArgs &a, int p)
     constexpr bool RING = STAGE && QBVH_ROW_STAGING && PHASE == 2;
     out.ring = RING ? st->ring + lane : nullptr;
     out.base = 0;
+    out.fill = 0;
     bool walked = PHASE != 1;
     bool elsewhere = false;   // particle of a sparse tree: walked by the leading blocks
     LJAcc acc;
@@ -1626,7 +1717,13 @@ __device__ __forceinline__ void warp_packet(const QueryArgs &a, int p)
         }
     }
     if (!walked) return;   // phase 1, no image to add for this warp: counts stay
-    if (RING && active && !elsewhere) out.drain();
+    if (RING) {
+        if (W == 1) {
+            if (active && !elsewhere) out.drain();
+        } else {
+            out.drain_group<W>(same, pidx, G, wsub);   // lanes pidx + m G, every lane together
+        }
+    }
     // the row index again (not kept live across the walk)
     int io = 0;
     if (active) {
