@@ -714,7 +714,7 @@ def run_fp64_comparison(args, local):
              ("WCA rho 0.8", 128_000, 0.8, workloads.WCA_RCUT, 0.0, half(0.8)),
              ("spinodal-like liquid/vapor", 1_000_000, 0.2, 3.0, 0.0, None),
              ("bench workload", 2_097_152, 0.8, 3.0, 0.3, 0.25)]
-    space = {_lib.QBVH_OPT_BUNDLE: [16, 32, 8], _lib.QBVH_OPT_NODE_FORMAT: [1, 0]}
+    space = {_lib.QBVH_OPT_BUNDLE: [64, 32, 16], _lib.QBVH_OPT_NODE_FORMAT: [0, 1]}
     out = []
     for label, n, rho, rc, skin, jit in cases:
         if jit is None:

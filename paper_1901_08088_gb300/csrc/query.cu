@@ -897,16 +897,17 @@ __device__ __forceinline__ bool cube_overlap(unsigned nlo, unsigned nhi, const L
 #ifndef QBVH_LOOP_COST
 #define QBVH_LOOP_COST 14
 #endif
-// the walks that filter bundles: exact lists of FP32 data with one particle per
-// lane, or 2 or 4 lanes per particle (those share a row through the staging
-// ring, so they need it, and the one-launch walk)
+// the walks that filter bundles: exact lists with one particle per lane (FP32
+// or double-precision data), or of FP32 data with 2 or 4 lanes per particle
+// (those share a row through the staging ring, so they need it, and the
+// one-launch walk)
 #ifndef QBVH_MULTI_LANE_FILTER
 #define QBVH_MULTI_LANE_FILTER 1
 #endif
 __host__ __device__ constexpr bool stage_on(int W, bool CAND, bool F64)
 {
-    return QBVH_PREFILTER && !CAND && !F64 &&
-           (W == 1 || (QBVH_MULTI_LANE_FILTER && (W == 2 || W == 4) && QBVH_ROW_STAGING &&
+    return QBVH_PREFILTER && !CAND &&
+           (W == 1 || (!F64 && QBVH_MULTI_LANE_FILTER && (W == 2 || W == 4) && QBVH_ROW_STAGING &&
                        !QBVH_QUERY_SPLIT_IMAGES));
 }
 
@@ -1027,9 +1028,27 @@ struct LJCtx {
 
 // Two survivors (x, y, z as packed pairs, original indices id) against the
 // lane's particle.
-template <bool SHIFT, bool SELF, bool LJ = false>
+// Z-order indices of a warp's survivors (double-precision data only): a
+// second array after the block's stages in dynamic shared memory.
+__device__ __forceinline__ const int *stage_zid(const BundleStage *st)
+{
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    return reinterpret_cast<const int *>(st - warp + nw) + warp * kStage;
+}
+
+// Double-precision data: the decision for a survivor (Z-order index j) whose
+// FP32 d2 lies inside the band around r^2 (see exact_d2_64).
+template <bool SHIFT>
+__device__ __forceinline__ bool band_decide(const QueryArgs &A, const Query &c, int j)
+{
+    return exact_d2_64<SHIFT>(A, c, j) < A.r2_64[c.pair];
+}
+
+template <bool SHIFT, bool SELF, bool LJ = false, bool F64 = false>
 __device__ __forceinline__ void survivor_vals(const Query &c, Row &out, const f32x2 X, const f32x2 Y, const f32x2 Z,
-                                              const int2 id, bool on, bool staged, const LJCtx &lj)
+                                              const int2 id, bool on, bool staged, const LJCtx &lj,
+                                              const QueryArgs *A = nullptr, const BundleStage *st = nullptr,
+                                              int t = 0)
 {
     f32x2 dx = f2_sub(X, f2_pack(c.xi, c.xi)), dy = f2_sub(Y, f2_pack(c.yi, c.yi)),
           dz = f2_sub(Z, f2_pack(c.zi, c.zi));
@@ -1044,8 +1063,23 @@ __device__ __forceinline__ void survivor_vals(const Query &c, Row &out, const f3
     f2_unpack(f2_mul(dz, dz), sz0, sz1);
     const float d0 = __fadd_rn(__fadd_rn(sx0, sy0), sz0);
     const float d1 = __fadd_rn(__fadd_rn(sx1, sy1), sz1);
-    const bool a0 = on && d0 < c.rl2 && (!SELF || id.x != c.self_id);
-    const bool a1 = on && d1 < c.rl2 && (!SELF || id.y != c.self_id);
+    bool a0, a1;
+    if (F64) {
+        // FP32 decides outside the band [rl2_lo, rl2_hi], FP64 inside it (rare)
+        const bool s0 = on && (!SELF || id.x != c.self_id), s1 = on && (!SELF || id.y != c.self_id);
+        a0 = s0 && d0 < c.rl2_lo;
+        a1 = s1 && d1 < c.rl2_lo;
+        const bool b0 = s0 && !(d0 < c.rl2_lo) && d0 <= c.rl2_hi;
+        const bool b1 = s1 && !(d1 < c.rl2_lo) && d1 <= c.rl2_hi;
+        if (b0 || b1) {
+            const int *zid = stage_zid(st);
+            if (b0) a0 = band_decide<SHIFT>(*A, c, zid[t]);
+            if (b1) a1 = band_decide<SHIFT>(*A, c, zid[t + 1]);
+        }
+    } else {
+        a0 = on && d0 < c.rl2 && (!SELF || id.x != c.self_id);
+        a1 = on && d1 < c.rl2 && (!SELF || id.y != c.self_id);
+    }
     if (LJ) {
         f32x2 vx = dx, vy = dy, vz = dz;
         float r0 = d0, r1 = d1;
@@ -1072,30 +1106,30 @@ __device__ __forceinline__ void survivor_vals(const Query &c, Row &out, const f3
 }
 
 // survivors t, t + 1 of the stage (8-byte loads)
-template <bool SHIFT, bool SELF, bool LJ = false>
+template <bool SHIFT, bool SELF, bool LJ = false, bool F64 = false>
 __device__ __forceinline__ void survivor_pair(const Query &c, Row &out, int t, bool on, const BundleStage *st,
-                                              bool staged, const LJCtx &lj = LJCtx{})
+                                              bool staged, const LJCtx &lj = LJCtx{}, const QueryArgs *A = nullptr)
 {
-    survivor_vals<SHIFT, SELF, LJ>(c, out, *reinterpret_cast<const f32x2 *>(st->x + t),
-                                   *reinterpret_cast<const f32x2 *>(st->y + t),
-                                   *reinterpret_cast<const f32x2 *>(st->z + t),
-                                   *reinterpret_cast<const int2 *>(st->id + t), on, staged, lj);
+    survivor_vals<SHIFT, SELF, LJ, F64>(c, out, *reinterpret_cast<const f32x2 *>(st->x + t),
+                                        *reinterpret_cast<const f32x2 *>(st->y + t),
+                                        *reinterpret_cast<const f32x2 *>(st->z + t),
+                                        *reinterpret_cast<const int2 *>(st->id + t), on, staged, lj, A, st, t);
 }
 
 // survivors t .. t + 3 of the stage, t a multiple of 4 (16-byte loads; each
 // half of a loaded float4 is an aligned register pair)
-template <bool SHIFT, bool SELF, bool LJ = false>
+template <bool SHIFT, bool SELF, bool LJ = false, bool F64 = false>
 __device__ __forceinline__ void survivor_quad(const Query &c, Row &out, int t, bool on, const BundleStage *st,
-                                              const LJCtx &lj)
+                                              const LJCtx &lj, const QueryArgs *A = nullptr)
 {
     const float4 X = *reinterpret_cast<const float4 *>(st->x + t);
     const float4 Y = *reinterpret_cast<const float4 *>(st->y + t);
     const float4 Z = *reinterpret_cast<const float4 *>(st->z + t);
     const int4 I = *reinterpret_cast<const int4 *>(st->id + t);
-    survivor_vals<SHIFT, SELF, LJ>(c, out, f2_pack(X.x, X.y), f2_pack(Y.x, Y.y), f2_pack(Z.x, Z.y),
-                                   make_int2(I.x, I.y), on, true, lj);
-    survivor_vals<SHIFT, SELF, LJ>(c, out, f2_pack(X.z, X.w), f2_pack(Y.z, Y.w), f2_pack(Z.z, Z.w),
-                                   make_int2(I.z, I.w), on, true, lj);
+    survivor_vals<SHIFT, SELF, LJ, F64>(c, out, f2_pack(X.x, X.y), f2_pack(Y.x, Y.y), f2_pack(Z.x, Z.y),
+                                        make_int2(I.x, I.y), on, true, lj, A, st, t);
+    survivor_vals<SHIFT, SELF, LJ, F64>(c, out, f2_pack(X.z, X.w), f2_pack(Y.z, Y.w), f2_pack(Z.z, Z.w),
+                                        make_int2(I.z, I.w), on, true, lj, A, st, t + 2);
 }
 
 // Every lane tests every survivor (one particle per lane), two per step: the
@@ -1106,25 +1140,27 @@ __device__ __forceinline__ void survivor_quad(const Query &c, Row &out, int t, b
 // of the N = 2M list differed at d = r_list.  Scalar add.rn is not contracted.)
 // With row staging the accepted entries are staged without a branch and the
 // completed sectors written once per 8 survivors and at the end.
-template <bool SHIFT, bool SELF, bool LJ = false>
+template <bool SHIFT, bool SELF, bool LJ = false, bool F64 = false>
 __device__ __forceinline__ void survivors_loop(const Query &c, Row &out, int s, bool on, const BundleStage *st,
-                                               const LJCtx &lj = LJCtx{})
+                                               const LJCtx &lj = LJCtx{}, const QueryArgs *A = nullptr)
 {
     const bool staged = out.ring != nullptr;
     int t = 0;
     if (staged) {
         for (; t + 8 <= s; t += 8) {
-            survivor_quad<SHIFT, SELF, LJ>(c, out, t, on, st, lj);
-            survivor_quad<SHIFT, SELF, LJ>(c, out, t + 4, on, st, lj);
+            survivor_quad<SHIFT, SELF, LJ, F64>(c, out, t, on, st, lj, A);
+            survivor_quad<SHIFT, SELF, LJ, F64>(c, out, t + 4, on, st, lj, A);
             out.check();
         }
     }
-    for (; t + 1 < s; t += 2) survivor_pair<SHIFT, SELF, LJ>(c, out, t, on, st, staged, lj);
+    for (; t + 1 < s; t += 2) survivor_pair<SHIFT, SELF, LJ, F64>(c, out, t, on, st, staged, lj, A);
     if (t < s) {
         const float4 q = make_float4(st->x[t], st->y[t], st->z[t], 0.f);
         const int id = st->id[t];
         const float d2 = exact_d2<SHIFT>(c, q);
-        const bool acc = on && d2 < c.rl2 && (!SELF || id != c.self_id);
+        bool acc = on && d2 < (F64 ? c.rl2_lo : c.rl2) && (!SELF || id != c.self_id);
+        if (F64 && on && (!SELF || id != c.self_id) && !(d2 < c.rl2_lo) && d2 <= c.rl2_hi)
+            acc = band_decide<SHIFT>(*A, c, stage_zid(st)[t]);
         if (LJ) lj_single<SHIFT>(*lj.acc, c, lj.sig2, lj.rc2, acc, d2, q);
         if (staged) out.stage(id, acc);
         else if (acc) out.push(id);
@@ -1246,6 +1282,7 @@ __device__ __forceinline__ void bundle_chunk(const QueryArgs &a, const Query &c,
 // The filter of a chunk of cnt <= 32 leaves starting at `first`: its
 // survivors are appended to the stage after the s already there; returns the
 // new count (warp-uniform).  Every lane of the warp calls this together.
+template <bool F64 = false>
 __device__ __forceinline__ int chunk_filter(const QueryArgs &a, int first, int cnt, float rs2, BundleStage *st,
                                             int s)
 {
@@ -1268,6 +1305,7 @@ __device__ __forceinline__ int chunk_filter(const QueryArgs &a, int first, int c
         st->y[r] = q.y;
         st->z[r] = q.z;
         st->id[r] = __float_as_int(q.w) & 0x7FFFFFFF;
+        if (F64) const_cast<int *>(stage_zid(st))[r] = first + lane;
     }
     return s + __popc(S);
 }
@@ -1278,7 +1316,7 @@ __device__ __forceinline__ int chunk_filter(const QueryArgs &a, int first, int c
 // distance overflows to +inf, so no lane accepts them, and their LJ terms are
 // zero.  (With the spread of few-lane bundles, a build option without row
 // staging, chunks are tested one at a time.)
-template <bool SHIFT, bool SELF, bool LJ = false, int W = 1>
+template <bool SHIFT, bool SELF, bool LJ = false, int W = 1, bool F64 = false>
 __device__ __forceinline__ void bundle_filtered(const QueryArgs &a, const Query &c, Row &out, int first, int cnt,
                                                 unsigned hm, bool on, float rs2, BundleStage *st,
                                                 const LJCtx &lj = LJCtx{}, int wsub = 0, unsigned same = 0u)
@@ -1290,7 +1328,8 @@ __device__ __forceinline__ void bundle_filtered(const QueryArgs &a, const Query 
         return;
     }
     int s = 0;
-    for (int base = 0; base < cnt; base += 32) s = chunk_filter(a, first + base, min(32, cnt - base), rs2, st, s);
+    for (int base = 0; base < cnt; base += 32)
+        s = chunk_filter<F64>(a, first + base, min(32, cnt - base), rs2, st, s);
     if (s == 0) return;
     const int pad = (2 * W - s % (2 * W)) % (2 * W);   // s <= 64, a multiple of 2 W: s + pad <= 64
     const int lane = threadIdx.x & 31;
@@ -1299,10 +1338,11 @@ __device__ __forceinline__ void bundle_filtered(const QueryArgs &a, const Query 
         st->y[s + lane] = 1e30f;
         st->z[s + lane] = 1e30f;
         st->id[s + lane] = 0;
+        if (F64) const_cast<int *>(stage_zid(st))[s + lane] = first;   // never read: +inf is outside the band
     }
     s += pad;
     __syncwarp();
-    if (W == 1) survivors_loop<SHIFT, SELF, LJ>(c, out, s, on, st, lj);
+    if (W == 1) survivors_loop<SHIFT, SELF, LJ, F64>(c, out, s, on, st, lj, &a);
     else survivors_loop_w<SHIFT, SELF, W>(c, out, s, on, st, wsub, same);
     __syncwarp();   // the next bundle rewrites the stage
 }
@@ -1391,11 +1431,11 @@ __device__ __forceinline__ void warp_walk(const QueryArgs &a, const Query &c, Ro
                         !SHIFT && __any_sync(FULL, (unsigned)(c.self - j) <= (unsigned)(l - j));
                     if (FILTER && l - j < 64) {
                         if (self_here)
-                            bundle_filtered<SHIFT, true, LJ, W>(a, c, out, j, l - j + 1, hm, on, rs2, st, lj, wsub,
-                                                                same);
+                            bundle_filtered<SHIFT, true, LJ, W, F64>(a, c, out, j, l - j + 1, hm, on, rs2, st, lj,
+                                                                     wsub, same);
                         else
-                            bundle_filtered<SHIFT, false, LJ, W>(a, c, out, j, l - j + 1, hm, on, rs2, st, lj, wsub,
-                                                                 same);
+                            bundle_filtered<SHIFT, false, LJ, W, F64>(a, c, out, j, l - j + 1, hm, on, rs2, st, lj,
+                                                                      wsub, same);
                     } else if (W == 1 && !CAND && l - j < 32 && __popc(hm) <= QBVH_SPREAD_MAX) {
                         if (self_here) bundle_spread<SHIFT, F64, true>(a, c, out, j, l - j + 1, hm);
                         else bundle_spread<SHIFT, F64, false>(a, c, out, j, l - j + 1, hm);
@@ -1804,6 +1844,18 @@ __global__ void QBVH_QUERY_BOUNDS query_warp_kernel(const __grid_constant__ Quer
     warp_query<WIDE, CAND, FMT, W, ONE, PHASE, F64, false, false>(a);
 }
 
+// Double-precision data: the filtered walk of one particle per lane, with its
+// own register cap (the FP64 band decision needs more registers than the
+// FP32 walk's 32)
+#ifndef QBVH_QUERY_F64_MIN_BLOCKS
+#define QBVH_QUERY_F64_MIN_BLOCKS 6
+#endif
+template <int FMT, bool ONE>
+__global__ void __launch_bounds__(256, QBVH_QUERY_F64_MIN_BLOCKS) query_f64_kernel(const __grid_constant__ QueryArgs a)
+{
+    warp_query<false, false, FMT, 1, ONE, 2, true, false, false>(a);
+}
+
 // the one-particle-per-lane walk of exact FP32 lists with the packet queue
 template <bool WIDE, int FMT, bool ONE>
 __global__ void QBVH_QUERY_BOUNDS query_queue_kernel(const __grid_constant__ QueryArgs a)
@@ -1850,9 +1902,10 @@ static int sparse_blocks_for(const QueryArgs &a)
 }
 
 // dynamic shared memory of a traversal block: one BundleStage per warp
-static size_t stage_bytes(int block, bool stage)
+static size_t stage_bytes(int block, bool stage, bool f64 = false)
 {
-    return stage ? (size_t)(block / 32) * sizeof(BundleStage) : 0;
+    // double-precision data: the survivors' Z-order indices after the stages
+    return stage ? (size_t)(block / 32) * (sizeof(BundleStage) + (f64 ? kStage * sizeof(int) : 0)) : 0;
 }
 
 // Blocks of `kernel` that one SM keeps resident at `block` threads and
@@ -1942,9 +1995,9 @@ static void launch_f64(const QueryArgs &a, cudaStream_t s)
 {
     const int b = a.block;
     const int grid = (int)(((long long)((a.n + 31) / 32) * 32 + b - 1) / b);
-    const size_t sm = stage_bytes(b, stage_on(1, false, true));
-    if (a.n_types == 1) query_warp_kernel<false, false, FMT, 1, true, 2, true><<<grid, b, sm, s>>>(a);
-    else query_warp_kernel<false, false, FMT, 1, false, 2, true><<<grid, b, sm, s>>>(a);
+    const size_t sm = stage_bytes(b, stage_on(1, false, true), true);
+    if (a.n_types == 1) query_f64_kernel<FMT, true><<<grid, b, sm, s>>>(a);
+    else query_f64_kernel<FMT, false><<<grid, b, sm, s>>>(a);
 }
 
 int query_lj_blocks(int n, int block)
