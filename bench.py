@@ -583,6 +583,7 @@ def run_batched(args, local):
 
     space = {k: autotune.OPTION_SPACE[k] for k in (_lib.QBVH_OPT_BUNDLE, _lib.QBVH_OPT_NODE_FORMAT,
                                                    _lib.QBVH_OPT_QUERY_BLOCK, _lib.QBVH_OPT_PERSISTENT)}
+    space[_lib.QBVH_OPT_WARP_PARTICLES] = [32, 16, 8]
     best, _, _ = autotune.tune(graph_step, space=space, reps=3, warmup=1, sweeps=1)
     g = runners[tuple(sorted(best.items()))]
     for x in runners.values():
@@ -592,6 +593,8 @@ def run_batched(args, local):
         assert g.run() == _lib.QBVH_OK
     reps = max(args.steps, 5)
     graph_ms = timed(lambda: (g.replay(), stream.synchronize(), g.status()), reps)
+    # the same batched launches issued eagerly: what the graph saves in launch overhead
+    eager_ms = timed(lambda: (g.enqueue_eager(), stream.synchronize(), g.status()), reps)
     loop = PerSystemLoop(buf, off, Ls, r, cap=g.cap, options=best, device=local)
     for _ in range(2):
         assert loop.run() == _lib.QBVH_OK
@@ -604,6 +607,7 @@ def run_batched(args, local):
         "graph_particles_per_s": total / (graph_ms * 1e-3),
         "loop_particles_per_s": total / (loop_ms * 1e-3),
         "graph_ms": graph_ms, "loop_ms": loop_ms, "ratio": loop_ms / graph_ms,
+        "eager_batched_ms": eager_ms, "eager_batched_particles_per_s": total / (eager_ms * 1e-3),
         "options": autotune.option_names(best),
     }
 

@@ -3,7 +3,7 @@
 ``BatchedNeighborList`` builds the trees of every system (one per system and
 type) and their neighbor lists with the library's batched build
 (``qbvh_build_batched``) and one traversal launch, captured once into a CUDA
-graph and replayed every step.  The graph ends with the 8-byte status copy;
+graph and replayed every step.  The graph ends with the 16-byte status copy;
 after a replay the host reads it and, if some row outgrew the capacity, raises
 the capacity and captures again (the tree is rebuilt inside the graph, so a
 replay always reflects the current positions in the input buffer).
@@ -77,6 +77,11 @@ class BatchedNeighborList:
         if self.graph is None:
             self.capture()
         self.graph.replay()
+
+    def enqueue_eager(self):
+        """The same build + query launched directly instead of from the graph
+        (no host wait); read the outcome with ``status`` after the stream has run."""
+        self._enqueue()
 
     def status(self) -> int:
         """After the stream has finished a replay: QBVH_OK, or grows cap and recaptures on overflow."""
