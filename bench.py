@@ -107,20 +107,20 @@ class ClockSampler:
 # options of each entry and the traversal sources whose SHA-256 prefix is given; any
 # other source or options report null.
 PROFILED_TRAFFIC = {
-    "source_sha256": "d2dc206a74618a72",
+    "source_sha256": "a353541e4b6bd59d",
     "entries": [
         {"options": {"bundle_k": 64, "node_format": 0, "traversal": 1, "warp_particles": 32, "query_block": 128,
                      "fused_lj": 0, "persistent": 0},
-         "bytes": 108.92e6 + 1007.33e6, "warp_inst": 1331763029},
+         "bytes": 108.99e6 + 1007.05e6, "warp_inst": 1336503541},
         {"options": {"bundle_k": 64, "node_format": 0, "traversal": 1, "warp_particles": 32, "query_block": 256,
                      "fused_lj": 0, "persistent": 0},
-         "bytes": 108.87e6 + 1006.62e6, "warp_inst": 1331763029},
+         "bytes": 108.88e6 + 1006.47e6, "warp_inst": 1336503565},
         {"options": {"bundle_k": 64, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 128,
                      "fused_lj": 0, "persistent": 0},
-         "bytes": 107.66e6 + 994.67e6, "warp_inst": 1297480446},
+         "bytes": 107.70e6 + 994.77e6, "warp_inst": 1302335900},
         {"options": {"bundle_k": 64, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256,
                      "fused_lj": 0, "persistent": 0},
-         "bytes": 107.64e6 + 994.48e6, "warp_inst": 1297480430},
+         "bytes": 108.33e6 + 994.71e6, "warp_inst": 1302335916},
     ],
 }
 # kernels of one timed step: build = prepare, Morton (+ sort histograms), segment
