@@ -1117,7 +1117,11 @@ __device__ __forceinline__ void survivor_pair(const Query &c, Row &out, int t, b
 }
 
 // survivors t .. t + 3 of the stage, t a multiple of 4 (16-byte loads; each
-// half of a loaded float4 is an aligned register pair)
+// half of a loaded float4 is an aligned register pair).  QBVH_SURVIVOR_QUAD = 0
+// loads two survivors at a time instead.
+#ifndef QBVH_SURVIVOR_QUAD
+#define QBVH_SURVIVOR_QUAD 1
+#endif
 template <bool SHIFT, bool SELF, bool LJ = false, bool F64 = false>
 __device__ __forceinline__ void survivor_quad(const Query &c, Row &out, int t, bool on, const BundleStage *st,
                                               const LJCtx &lj, const QueryArgs *A = nullptr)
@@ -1148,8 +1152,15 @@ __device__ __forceinline__ void survivors_loop(const Query &c, Row &out, int s, 
     int t = 0;
     if (staged) {
         for (; t + 8 <= s; t += 8) {
+#if QBVH_SURVIVOR_QUAD
             survivor_quad<SHIFT, SELF, LJ, F64>(c, out, t, on, st, lj, A);
             survivor_quad<SHIFT, SELF, LJ, F64>(c, out, t + 4, on, st, lj, A);
+#else
+            survivor_pair<SHIFT, SELF, LJ, F64>(c, out, t, on, st, true, lj, A);
+            survivor_pair<SHIFT, SELF, LJ, F64>(c, out, t + 2, on, st, true, lj, A);
+            survivor_pair<SHIFT, SELF, LJ, F64>(c, out, t + 4, on, st, true, lj, A);
+            survivor_pair<SHIFT, SELF, LJ, F64>(c, out, t + 6, on, st, true, lj, A);
+#endif
             out.check();
         }
     }
