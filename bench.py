@@ -107,20 +107,20 @@ class ClockSampler:
 # options of each entry and the traversal sources whose SHA-256 prefix is given; any
 # other source or options report null.
 PROFILED_TRAFFIC = {
-    "source_sha256": "a353541e4b6bd59d",
+    "source_sha256": "ba179f7ae5a5ff5c",
     "entries": [
         {"options": {"bundle_k": 64, "node_format": 0, "traversal": 1, "warp_particles": 32, "query_block": 128,
                      "fused_lj": 0, "persistent": 0},
-         "bytes": 108.99e6 + 1007.05e6, "warp_inst": 1336503541},
+         "bytes": 109.72e6 + 1007.59e6, "warp_inst": 1336503549},
         {"options": {"bundle_k": 64, "node_format": 0, "traversal": 1, "warp_particles": 32, "query_block": 256,
                      "fused_lj": 0, "persistent": 0},
-         "bytes": 108.88e6 + 1006.47e6, "warp_inst": 1336503565},
+         "bytes": 108.79e6 + 1006.68e6, "warp_inst": 1336503581},
         {"options": {"bundle_k": 64, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 128,
                      "fused_lj": 0, "persistent": 0},
-         "bytes": 107.70e6 + 994.77e6, "warp_inst": 1302335900},
+         "bytes": 107.69e6 + 994.58e6, "warp_inst": 1302335900},
         {"options": {"bundle_k": 64, "node_format": 1, "traversal": 1, "warp_particles": 32, "query_block": 256,
                      "fused_lj": 0, "persistent": 0},
-         "bytes": 108.33e6 + 994.71e6, "warp_inst": 1302335916},
+         "bytes": 107.69e6 + 994.40e6, "warp_inst": 1302335932},
     ],
 }
 # kernels of one timed step: build = prepare, Morton (+ sort histograms), segment
