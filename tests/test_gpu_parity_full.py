@@ -2,10 +2,10 @@
 
 * The N = 2,097,152 fluid (the benchmark's workload): every one of the 2M
   rows against the oracle's cell list, under the options the benchmark's
-  autotuner picks (K = 32, 256-thread blocks, FP32 nodes), under the paper's
-  10-bit quantized nodes, and under the one-thread-per-particle walk of
-  Alg. 1 as written; plus the FP64 band check of the FP32 decision on a
-  sample.
+  autotuner picks (K = 64, 128-thread blocks, 10-bit quantized nodes; earlier
+  K = 32 with FP32 nodes), under every node format, with two and four lanes
+  per particle, and under the one-thread-per-particle walk of Alg. 1 as
+  written; plus the FP64 band check of the FP32 decision on a sample.
 * The differentiable two-type workload (32 systems x 65,536 particles, one
   batched build): every row of every system against the oracle of that
   system alone, with one tree per type (the paper's layout, Sec. 1 and 5) and
@@ -40,8 +40,11 @@ def fluid_2m():
     dict(bundle=16, block=128, node_format=1, traversal=1, warp_particles=16),   # two lanes per particle
     dict(bundle=64, block=256, node_format=0, traversal=1, warp_particles=32),   # 64-leaf bundles
     dict(bundle=64, block=256, node_format=2, traversal=1, warp_particles=32),   # 21-bit nodes
+    dict(bundle=64, block=128, node_format=0, traversal=1, warp_particles=32),   # the benchmark's current choice
+    dict(bundle=64, block=128, node_format=1, traversal=1, warp_particles=32),   # FP32 nodes, 64-leaf bundles
+    dict(bundle=64, block=128, node_format=0, traversal=1, warp_particles=8),    # four lanes per particle, filtered
 ], ids=["bench_fp32_nodes", "quantized_nodes", "thread_per_particle", "two_lanes_per_particle", "bundles_64",
-        "nodes_21bit"])
+        "nodes_21bit", "bench_current", "fp32_nodes_64", "four_lanes_per_particle"])
 def test_all_2m_rows_equal_cell_list(fluid_2m, opts):
     import torch
 
