@@ -33,6 +33,9 @@ constexpr int kLJParticles = QBVH_LJ_PARTICLES;   // particles per block, taken 
 #define QBVH_LJ_MIN_BLOCKS_ONE 9
 #endif
 // row entries per load: 4 (16 bytes; 2 measured 0.74 -> 0.83 ms)
+#ifndef QBVH_LJ_PREFETCH
+#define QBVH_LJ_PREFETCH 1
+#endif
 #ifndef QBVH_LJ_VEC
 #define QBVH_LJ_VEC 4
 #endif
@@ -77,10 +80,23 @@ lj_forward_kernel(const __grid_constant__ LJArgs a)
             // 16- or 8-byte load (rows are 16-byte aligned: the capacity is a
             // multiple of 4), then their positions, then does the arithmetic
             constexpr int V = QBVH_LJ_VEC;
+            // with 4 entries per load the next chunk's entries are loaded one
+            // iteration ahead (QBVH_LJ_PREFETCH), so that a row load is in
+            // flight while the current chunk's positions are gathered
+            int4 vnext = make_int4(-1, -1, -1, -1);
+            if (QBVH_LJ_PREFETCH && V == 4 && V * sub < c)
+                vnext = __ldg(reinterpret_cast<const int4 *>(row) + ((V * sub) >> 2));
             for (int k0 = V * sub; k0 < c; k0 += V * TPP) {
                 int jj[V];
                 if (V == 4) {
-                    const int4 v = __ldg(reinterpret_cast<const int4 *>(row) + (k0 >> 2));
+                    int4 v;
+                    if (QBVH_LJ_PREFETCH) {
+                        v = vnext;
+                        const int kn = k0 + V * TPP;
+                        if (kn < c) vnext = __ldg(reinterpret_cast<const int4 *>(row) + (kn >> 2));
+                    } else {
+                        v = __ldg(reinterpret_cast<const int4 *>(row) + (k0 >> 2));
+                    }
                     jj[0] = v.x;
                     jj[V > 1 ? 1 : 0] = v.y;
                     jj[V > 2 ? 2 : 0] = v.z;
